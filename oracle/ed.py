@@ -1,0 +1,136 @@
+"""Fock-space exact diagonalisation of the Hubbard Hamiltonian of Eq. HubbModel
+for small clusters, used to pin the oracle's weights and Wick contractions.
+
+Two forms:
+  * ``trotter_averages``: the Trotterised density matrix
+    rho = (e^{-dtau H0/2} e^{-dtau H_U} e^{-dtau H0/2})^M  (Sec. II.B 'First'),
+    which the Hubbard-Stratonovich sum reproduces exactly at any dtau;
+  * ``thermal_averages``: exact e^{-beta H} by full diagonalisation (tiny clusters).
+
+Each (N_up, N_dn) sector is the tensor product V_up x V_dn of one-species Fock
+spaces; a state is a pair of bit masks, fermion signs by Jordan-Wigner order
+(site index), all up operators ordered before all down operators.
+"""
+import itertools
+import numpy as np
+import scipy.linalg as sla
+
+
+def species_basis(N, n):
+    states = [sum(1 << i for i in c) for c in itertools.combinations(range(N), n)]
+    return states, {s: a for a, s in enumerate(states)}
+
+
+def species_hopping(K, states, index):
+    """Matrix of sum_ij K_ij c_i^+ c_j in the fixed-particle-number basis."""
+    N = K.shape[0]
+    d = len(states)
+    H = np.zeros((d, d), dtype=K.dtype)
+    for a, s in enumerate(states):
+        for j in range(N):
+            if not (s >> j) & 1:
+                continue
+            s1 = s ^ (1 << j)
+            sg1 = (-1) ** bin(s & ((1 << j) - 1)).count("1")
+            for i in range(N):
+                if K[i, j] == 0 or (s1 >> i) & 1:
+                    continue
+                s2 = s1 | (1 << i)
+                sg2 = (-1) ** bin(s1 & ((1 << i) - 1)).count("1")
+                H[index[s2], a] += K[i, j] * sg1 * sg2
+    return H
+
+
+def occupations(states, N):
+    return np.array([[(s >> i) & 1 for i in range(N)] for s in states], dtype=float)
+
+
+def _sector_data(K, N, nu, nd):
+    su, iu = species_basis(N, nu)
+    sd, idd = species_basis(N, nd)
+    return (species_hopping(K, su, iu), species_hopping(K, sd, idd),
+            occupations(su, N), occupations(sd, N))
+
+
+def _observables_diag(occ_u, occ_d, U, bravais_pairs):
+    """Diagonal observables on the product basis, arrays of shape (du, dd)."""
+    nu = occ_u[:, None, :]
+    nd = occ_d[None, :, :]
+    docc = (nu * nd).sum(axis=2)                       # sum_i n_i_up n_i_dn
+    hu = U * (nu * nd - 0.5 * (nu + nd)).sum(axis=2)  # H_U eigenvalues
+    sz = 0.5 * (nu - nd)                                # (du, dd, N)
+    czz = {key: sum((sz[..., i] * sz[..., j]) for i, j in pairs) for key, pairs in bravais_pairs.items()}
+    return docc, hu, czz
+
+
+def bravais_pair_table(lat):
+    """For C_zz(r): r=(d1,d2) -> list of site pairs (i, i+r) on the same sublattice."""
+    out = {}
+    for d2 in range(lat.L2):
+        for d1 in range(lat.L1):
+            pairs = []
+            for sub in (0, 1):
+                for n2 in range(lat.L2):
+                    for n1 in range(lat.L1):
+                        pairs.append((lat.site(sub, n1, n2), lat.site(sub, n1 + d1, n2 + d2)))
+            out[(d1, d2)] = pairs
+    return out
+
+
+def trotter_averages(lat, K, U, dtau, M):
+    """<D>, <e>, C_zz under the Trotterised density matrix (exact for the HS sum)."""
+    N = lat.N
+    pairs = bravais_pair_table(lat)
+    Z = 0.0
+    acc_d = acc_kin = 0.0
+    acc_c = {k: 0.0 for k in pairs}
+    for nu in range(N + 1):
+        for nd in range(N + 1):
+            Ku, Kd, ou, od = _sector_data(K, N, nu, nd)
+            du, dd = Ku.shape[0], Kd.shape[0]
+            Su = sla.expm(-0.5 * dtau * Ku)
+            Sd = sla.expm(-0.5 * dtau * Kd)
+            docc, hu, czz = _observables_diag(ou, od, U, pairs)
+            eU = np.exp(-dtau * hu)
+            X = np.eye(du * dd).reshape(du, dd, du * dd)
+            for _ in range(M):
+                X = np.tensordot(Su, X, axes=(1, 0))
+                X = np.matmul(Sd, X)
+                X = eU[:, :, None] * X
+                X = np.tensordot(Su, X, axes=(1, 0))
+                X = np.matmul(Sd, X)
+            ia, ib = np.divmod(np.arange(du * dd), dd)
+            diag = X[ia, ib, np.arange(du * dd)].reshape(du, dd)
+            Z += diag.sum()
+            acc_d += (docc * diag).sum()
+            for key in pairs:
+                acc_c[key] += (czz[key] * diag).sum()
+            KX = np.tensordot(Ku, X, axes=(1, 0)) + np.matmul(Kd, X)
+            acc_kin += KX[ia, ib, np.arange(du * dd)].sum()
+    D = acc_d / Z / N
+    ekin = acc_kin / Z
+    Czz = np.zeros((lat.L2, lat.L1))
+    for (d1, d2), v in acc_c.items():
+        Czz[d2, d1] = v / Z / (2.0 * lat.Nc)
+    return dict(double_occ=D, energy=(ekin + N * U * D) / N, ekin=ekin / N, Czz=Czz)
+
+
+def thermal_averages(lat, K, U, beta):
+    """Exact thermal <D> and <e> by full diagonalisation (only for tiny N)."""
+    N = lat.N
+    Z = acc_d = acc_kin = 0.0
+    for nu in range(N + 1):
+        for nd in range(N + 1):
+            Ku, Kd, ou, od = _sector_data(K, N, nu, nd)
+            du, dd = Ku.shape[0], Kd.shape[0]
+            docc, hu, _ = _observables_diag(ou, od, U, {})
+            H0 = np.kron(Ku, np.eye(dd)) + np.kron(np.eye(du), Kd)
+            H = H0 + np.diag(hu.reshape(-1))
+            w, V = np.linalg.eigh(H)
+            p = np.exp(-beta * w)
+            Z += p.sum()
+            acc_d += np.einsum("n,in,i,in->", p, V, docc.reshape(-1), V)
+            acc_kin += np.einsum("n,in,ij,jn->", p, V, H0, V)
+    D = acc_d / Z / N
+    ekin = acc_kin / Z
+    return dict(double_occ=D, energy=(ekin + N * U * D) / N, ekin=ekin / N)

@@ -1,0 +1,39 @@
+"""Seeded synthetic inputs shared by the oracle-side tests, the CUDA-side tests and bench.py.
+
+This module holds none of the method's arithmetic: it only defines the workload
+shapes (lattice size, temperature, Trotter step, interaction, delay rank,
+stabilisation period) and draws seeded random inputs (Ising field
+configurations, dense test matrices).  Both the CPU oracle and the CUDA path
+consume these inputs; neither side's numerics live here.
+"""
+import numpy as np
+
+# The five workload configurations (honeycomb Hubbard model, t = 1, half filling,
+# periodic boundaries, spin-channel Ising Hubbard-Stratonovich field).
+WORKLOADS = {
+    # small case the oracle finishes in seconds
+    "L3_beta3": dict(L=3, beta=3.0, dtau=0.1, U=3.73, n_delay=4, n_stab=10),
+    # GPU plain FP64 case (three interaction strengths are run in the tests)
+    "L6_beta6": dict(L=6, beta=6.0, dtau=0.1, U=3.73, n_delay=32, n_stab=10),
+    # the headline sweep workload: N = 1152 sites, M = 240 slices
+    "L24_beta24": dict(L=24, beta=24.0, dtau=0.1, U=3.73, n_delay=64, n_stab=8),
+}
+
+
+def n_slices(beta, dtau):
+    m = int(round(beta / dtau))
+    if abs(m * dtau - beta) > 1e-9:
+        raise ValueError("beta must be an integer multiple of dtau")
+    return m
+
+
+def random_field(M, N, seed):
+    """Uniform i.i.d. Ising field s[l, i] in {+1, -1}, shape (M, N), int8."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.where(rng.random((M, N)) < 0.5, 1, -1).astype(np.int8)
+
+
+def random_matrix(N, seed, scale=1.0):
+    """Dense float64 N x N matrix with entries uniform in [-scale, scale)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return (2.0 * rng.random((N, N)) - 1.0) * scale
