@@ -1,0 +1,183 @@
+/*
+ * afqmc.h -- C ABI of libafqmc.so: the Monte Carlo sweep of finite-temperature
+ * auxiliary-field QMC (DQMC) for the half-filled honeycomb Hubbard model on an
+ * L1 x L2 two-sublattice lattice, run on one CUDA GPU (sm_103a).
+ *
+ * The method is the one of "Finite-temperature quantum Monte Carlo study of
+ * Dirac quantum criticality: Algorithmic advances and comprehensive analysis":
+ *   - model and Trotter/HS decomposition: Sec. II.A-B, Eqs. HubbModel, SzHS,
+ *     coupling, ConfgWeight, GrFMat;
+ *   - propagation G -> B G B^-1 with e^{-dtau K} applied in momentum space,
+ *     one 2x2 Bloch block per k: Sec. III.A, Eqs. NewBlMat, ExpLambda,
+ *     FourierMat, ColumnDem;
+ *   - Metropolis updates with determinant ratios and the delayed rank-k
+ *     Green's-function update: Sec. III.B, Eqs. DetailBalance, DRatio,
+ *     rRatioLocal, DelayG0, DelayRatio, DelayRgenk, FinalDelay;
+ *   - periodic QR stabilisation of the propagator chains: Sec. II.B ('Second');
+ *   - equal-time observables: Sec. II.C, App. C.
+ *
+ * Conventions shared by every entry point
+ *   - Sites: N = 2*L1*L2.  Index i < Nc = L1*L2 is sublattice A, i >= Nc is B;
+ *     within a sublattice the cell r = n1 a1 + n2 a2 has index n1 + L1*n2.
+ *   - Slices l = 1..M, M = beta/dtau.  Field s[l-1][i] in {+1,-1}, int8,
+ *     slice-major (M*N bytes).
+ *   - Matrices are FP64, row-major, N*N, G[i][j] = <c_i c_j^+> of spin up.
+ *   - Host pointers are owned by the caller and only read/written during the
+ *     call; the library owns all device memory it allocates in afqmc_create.
+ *   - All work is enqueued on the stream given to afqmc_create; calls that
+ *     return host data synchronise that stream.
+ *   - No C++ exception crosses this boundary.  A non-OK status leaves a message
+ *     retrievable with afqmc_last_error(handle).  Numeric failures (NaN/Inf)
+ *     and device-side wait timeouts return a status; nothing traps.
+ *
+ * Scope of this version: periodic boundaries (theta = 0), the spin-channel
+ * field (hs_channel = 0), one Markov chain per handle; the real FP64 path.
+ */
+#ifndef AFQMC_H
+#define AFQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct afqmc_handle afqmc_handle;
+
+typedef enum {
+    AFQMC_OK = 0,
+    AFQMC_E_INVALID = 1,     /* bad argument or unsupported parameter combination */
+    AFQMC_E_NOMEM = 2,       /* device or host allocation failed */
+    AFQMC_E_CUDA = 3,        /* a CUDA runtime call failed */
+    AFQMC_E_NUMERIC = 4,     /* NaN/Inf in G or in a ratio */
+    AFQMC_E_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    AFQMC_E_STATE = 6        /* handle unusable after an earlier error */
+} afqmc_status;
+
+/* Simulation parameters (Sec. II.A-B; Sec. III.B for n_delay). */
+typedef struct {
+    int32_t L1, L2;        /* unit cells along a1, a2 (>= 1) */
+    double t;              /* hopping amplitude */
+    double U;              /* Hubbard repulsion (>= 0) */
+    double beta, dtau;     /* M = beta/dtau must be an integer (|M dtau - beta| < 1e-9) */
+    double theta1, theta2; /* twist angles in units of 2 pi; must be 0 in this version */
+    int32_t hs_channel;    /* 0 = spin channel HS-s^z (Eq. SzHS); only 0 supported */
+    int32_t n_delay;       /* delay rank n_d >= 1; 1 is the local Sherman-Morrison update */
+    int32_t n_stab;        /* slices between QR recomputations of G; M % n_stab == 0 */
+    int32_t precision;     /* 0 = FP64 everywhere (only 0 supported) */
+    int32_t measure;       /* 1: accumulate observables at every recomputation of G in a sweep */
+    int32_t chain;         /* chain index: selects the random stream */
+    int32_t device;        /* CUDA device ordinal */
+    uint64_t seed;         /* random seed; also draws the initial field */
+} afqmc_params;
+
+/* Counters of the sweeps done by one afqmc_sweep call. */
+typedef struct {
+    uint64_t proposed;      /* single-site flips proposed (2*N*M per sweep) */
+    uint64_t accepted;      /* flips accepted */
+    double max_stab_drift;  /* max |G_wrapped - G_recomputed| over recomputations */
+    uint64_t launches;      /* CUDA kernels launched by the call */
+} afqmc_sweep_stats;
+
+/* Per-kernel-family launch counts and device times (CUDA events on the
+ * handle's stream), accumulated while timing is enabled. */
+enum {
+    AFQMC_K_PROPAGATE = 0,  /* momentum-space propagation rows (wrap, chain products, half step) */
+    AFQMC_K_UPDATE = 1,     /* delayed-update slice kernel (proposals, x/y recursion, flush) */
+    AFQMC_K_QR = 2,         /* Householder QR */
+    AFQMC_K_GEMM = 3,       /* FP64 GEMM */
+    AFQMC_K_QRAUX = 4,      /* Q formation, Q^T application, back substitution, pivoting */
+    AFQMC_K_MEASURE = 5,    /* observables */
+    AFQMC_K_MISC = 6,       /* copies of identity, drift check, small helpers */
+    AFQMC_K_COUNT = 7
+};
+typedef struct {
+    uint64_t launches[AFQMC_K_COUNT];
+    double ms[AFQMC_K_COUNT];
+} afqmc_timing;
+
+/* Equal-time observables (Sec. II.C; App. C).  Averages over n_samples measurements. */
+typedef struct {
+    double energy;      /* e = (<H0> + N U D) / N                          (App. C) */
+    double double_occ;  /* D = N^-1 sum_i <n_i_up n_i_dn>                   (Sec. II.C) */
+    double ekin;        /* <H0> / N */
+    double density;     /* N^-1 sum_i <n_i> (1 at half filling) */
+    double m2;          /* S_zz(Gamma) / (2 Nc)                             (Eq. SpinStrucF) */
+    double S_af;        /* S_zz(Gamma) */
+    double S_af_dk;     /* S_zz(Gamma + b1/L1) */
+    double R_m2;        /* 1 - S_zz(Gamma + b1/L1) / S_zz(Gamma)            (Eq. CrfRatio) */
+    double Czz_half;    /* C_zz(r = floor(L1/2) a1)                         (Eq. SzSzCrF) */
+    int64_t n_samples;
+} afqmc_obs;
+
+/* Create a chain: builds the lattice, the 2x2 Bloch propagator blocks
+ * e^{-+dtau h(k)}, e^{-+dtau h(k)/2} (Eq. ExpLambda), draws the initial field
+ * from (seed, chain), builds the QR-stabilised propagator stacks and G at
+ * slice 0.  cuda_stream: a cudaStream_t (e.g. torch.cuda.Stream.cuda_stream) or
+ * NULL for a stream owned by the handle.  *out is NULL on failure. */
+afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle** out);
+
+/* Release all device memory of the handle.  NULL is allowed. */
+afqmc_status afqmc_destroy(afqmc_handle* h);
+
+/* Replace the field (host, M*N int8, entries must be +1 or -1; otherwise
+ * AFQMC_E_INVALID and the handle is unchanged), rebuild the stacks and G at
+ * slice 0, reset the sweep counter to sweep_index. */
+afqmc_status afqmc_set_field(afqmc_handle* h, const int8_t* s_host, uint64_t sweep_index);
+
+/* Copy the current field to host (M*N int8). */
+afqmc_status afqmc_get_field(afqmc_handle* h, int8_t* s_host);
+
+/* Run n_sweeps sweeps (Sec. III.A: a forward pass l = 1..M and a backward pass
+ * l = M..1; in each slice every site i = 0..N-1 is proposed once, accepted iff
+ * u < e^{2 gamma s_i} r^2 with r = 1 + Delta (1 - G_ii), using the delayed
+ * update of rank n_delay; G recomputed every n_stab slices).  stats may be NULL. */
+afqmc_status afqmc_sweep(afqmc_handle* h, int32_t n_sweeps, afqmc_sweep_stats* stats);
+
+/* Measure the current G (the slice the chain is at: slice 0 between sweeps) now.
+ * Czz (Nc doubles, order d1 + L1*d2) and nk (Nc*2*2 complex, interleaved
+ * re,im, order (l1 + L1*l2)*4 + 2*a + b, n_ab(k) of Eq. nkMatrix) may be NULL. */
+afqmc_status afqmc_measure(afqmc_handle* h, afqmc_obs* out, double* Czz, double* nk);
+
+/* Averages of the measurements accumulated during sweeps since the last call
+ * (params.measure = 1), then reset.  n_samples = 0 if none.  Arrays as above. */
+afqmc_status afqmc_get_obs(afqmc_handle* h, afqmc_obs* out, double* Czz, double* nk);
+
+/* G at slice l (0 <= l <= M) recomputed from scratch for the current field by
+ * QR-stabilised chains (Eq. GrFMat); written to out (host, N*N).  Observer path. */
+afqmc_status afqmc_get_G(afqmc_handle* h, int32_t slice, double* out);
+
+/* Propagate a host matrix with the current field (Sec. III.A): direction +1
+ * computes B_l A B_l^-1, -1 computes B_l^-1 A B_l; 0 computes the half step
+ * e^{-dtau K/2} A e^{+dtau K/2} used for measurements.  In place on A (N*N). */
+afqmc_status afqmc_wrap_matrix(afqmc_handle* h, int32_t slice, int32_t direction, double* A);
+
+/* Delayed update of slice l on a given G (host, N*N, in/out), pass 0 or 1, with
+ * the random numbers of sweep number sweep_index; updates the handle's field
+ * for slice l and returns the accepted count in *n_accepted (may be NULL). */
+afqmc_status afqmc_update_slice(afqmc_handle* h, int32_t slice, int32_t pass,
+                                uint64_t sweep_index, double* G, int32_t* n_accepted);
+
+/* Weight ratio of flipping s[l-1][i] (Eqs. DRatio, rRatioLocal with the
+ * particle-hole factor): out[0] = R = e^{2 gamma s} r^2, out[1] = r, using G at
+ * slice l recomputed from scratch. */
+afqmc_status afqmc_det_ratio(afqmc_handle* h, int32_t slice, int32_t site, double out[2]);
+
+/* Enable (1) or disable (0) per-launch CUDA-event timing; resets the totals. */
+afqmc_status afqmc_set_timing(afqmc_handle* h, int32_t enable);
+
+/* Totals since afqmc_set_timing (synchronises the stream). */
+afqmc_status afqmc_get_timing(afqmc_handle* h, afqmc_timing* out);
+
+/* Sizes of the handle: N, M, Nc. */
+afqmc_status afqmc_dims(const afqmc_handle* h, int32_t* N, int32_t* M, int32_t* Nc);
+
+/* Message of the last failed call on h (never NULL).  With h == NULL: the last
+ * afqmc_create failure of this thread. */
+const char* afqmc_last_error(const afqmc_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFQMC_H */

@@ -1,0 +1,241 @@
+"""Python binding of libafqmc.so (include/afqmc.h): argument marshalling only.
+
+Every computation runs in the CUDA kernels of the library; importing this
+module fails loudly when the library is missing.  The functions carry the
+names of the C entry points; ``Chain`` is a small convenience wrapper.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libafqmc.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libafqmc.so is not built: run `python -m paper_2609_14668_b300.build` (nvcc, sm_103a)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+STATUS = {0: "AFQMC_OK", 1: "AFQMC_E_INVALID", 2: "AFQMC_E_NOMEM", 3: "AFQMC_E_CUDA",
+          4: "AFQMC_E_NUMERIC", 5: "AFQMC_E_TIMEOUT", 6: "AFQMC_E_STATE"}
+
+
+class afqmc_params(ctypes.Structure):
+    _fields_ = [("L1", ctypes.c_int32), ("L2", ctypes.c_int32), ("t", ctypes.c_double), ("U", ctypes.c_double),
+                ("beta", ctypes.c_double), ("dtau", ctypes.c_double), ("theta1", ctypes.c_double),
+                ("theta2", ctypes.c_double), ("hs_channel", ctypes.c_int32), ("n_delay", ctypes.c_int32),
+                ("n_stab", ctypes.c_int32), ("precision", ctypes.c_int32), ("measure", ctypes.c_int32),
+                ("chain", ctypes.c_int32), ("device", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class afqmc_sweep_stats(ctypes.Structure):
+    _fields_ = [("proposed", ctypes.c_uint64), ("accepted", ctypes.c_uint64), ("max_stab_drift", ctypes.c_double),
+                ("launches", ctypes.c_uint64)]
+
+
+KERNEL_FAMILIES = ["propagate", "update", "qr", "gemm", "qr_aux", "measure", "misc"]
+
+
+class afqmc_timing(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64 * 7), ("ms", ctypes.c_double * 7)]
+
+
+class afqmc_obs(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("double_occ", ctypes.c_double), ("ekin", ctypes.c_double),
+                ("density", ctypes.c_double), ("m2", ctypes.c_double), ("S_af", ctypes.c_double),
+                ("S_af_dk", ctypes.c_double), ("R_m2", ctypes.c_double), ("Czz_half", ctypes.c_double),
+                ("n_samples", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_H = ctypes.c_void_p
+_P = ctypes.POINTER
+_DP = _P(ctypes.c_double)
+_I8P = _P(ctypes.c_int8)
+
+_SIGS = {
+    "afqmc_create": ([_P(afqmc_params), ctypes.c_void_p, _P(_H)]),
+    "afqmc_destroy": ([_H]),
+    "afqmc_set_field": ([_H, _I8P, ctypes.c_uint64]),
+    "afqmc_get_field": ([_H, _I8P]),
+    "afqmc_sweep": ([_H, ctypes.c_int32, _P(afqmc_sweep_stats)]),
+    "afqmc_measure": ([_H, _P(afqmc_obs), _DP, _DP]),
+    "afqmc_get_obs": ([_H, _P(afqmc_obs), _DP, _DP]),
+    "afqmc_get_G": ([_H, ctypes.c_int32, _DP]),
+    "afqmc_wrap_matrix": ([_H, ctypes.c_int32, ctypes.c_int32, _DP]),
+    "afqmc_update_slice": ([_H, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _DP, _P(ctypes.c_int32)]),
+    "afqmc_det_ratio": ([_H, ctypes.c_int32, ctypes.c_int32, _DP]),
+    "afqmc_dims": ([_H, _P(ctypes.c_int32), _P(ctypes.c_int32), _P(ctypes.c_int32)]),
+    "afqmc_set_timing": ([_H, ctypes.c_int32]),
+    "afqmc_get_timing": ([_H, _P(afqmc_timing)]),
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+_lib.afqmc_last_error.argtypes = [_H]
+_lib.afqmc_last_error.restype = ctypes.c_char_p
+
+EXPORTED = sorted(list(_SIGS) + ["afqmc_last_error"])
+
+
+class AfqmcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(code, handle):
+    if code != 0:
+        msg = _lib.afqmc_last_error(handle)
+        raise AfqmcError(code, msg.decode() if msg else "")
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_DP)
+
+
+# ----------------------------------------------------------------- C names
+def afqmc_create(params, stream=None):
+    h = _H()
+    code = _lib.afqmc_create(ctypes.byref(params), ctypes.c_void_p(stream or 0), ctypes.byref(h))
+    _check(code, None)
+    return h
+
+
+def afqmc_destroy(h):
+    _check(_lib.afqmc_destroy(h), h)
+
+
+def afqmc_dims(h):
+    N, M, Nc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.afqmc_dims(h, ctypes.byref(N), ctypes.byref(M), ctypes.byref(Nc)), h)
+    return N.value, M.value, Nc.value
+
+
+def afqmc_set_field(h, field, sweep_index=0):
+    f = np.ascontiguousarray(field, dtype=np.int8)
+    _check(_lib.afqmc_set_field(h, f.ctypes.data_as(_I8P), sweep_index), h)
+
+
+def afqmc_get_field(h):
+    N, M, _ = afqmc_dims(h)
+    f = np.empty((M, N), dtype=np.int8)
+    _check(_lib.afqmc_get_field(h, f.ctypes.data_as(_I8P)), h)
+    return f
+
+
+def afqmc_sweep(h, n_sweeps=1):
+    st = afqmc_sweep_stats()
+    _check(_lib.afqmc_sweep(h, n_sweeps, ctypes.byref(st)), h)
+    return st
+
+
+def _obs_call(fn, h):
+    N, M, Nc = afqmc_dims(h)
+    o = afqmc_obs()
+    czz = np.empty(Nc)
+    nk = np.empty(8 * Nc)
+    _check(fn(h, ctypes.byref(o), _dptr(czz), _dptr(nk)), h)
+    d = o.as_dict()
+    d["Czz"] = czz
+    d["nk"] = nk.view(np.complex128).reshape(Nc, 2, 2)
+    return d
+
+
+def afqmc_measure(h):
+    return _obs_call(_lib.afqmc_measure, h)
+
+
+def afqmc_get_obs(h):
+    return _obs_call(_lib.afqmc_get_obs, h)
+
+
+def afqmc_get_G(h, slice_):
+    N, _, _ = afqmc_dims(h)
+    G = np.empty((N, N))
+    _check(_lib.afqmc_get_G(h, slice_, _dptr(G)), h)
+    return G
+
+
+def afqmc_wrap_matrix(h, slice_, direction, A):
+    B = np.array(A, dtype=np.float64, order="C", copy=True)
+    _check(_lib.afqmc_wrap_matrix(h, slice_, direction, _dptr(B)), h)
+    return B
+
+
+def afqmc_update_slice(h, slice_, pas, sweep_index, G):
+    B = np.array(G, dtype=np.float64, order="C", copy=True)
+    n = ctypes.c_int32()
+    _check(_lib.afqmc_update_slice(h, slice_, pas, sweep_index, _dptr(B), ctypes.byref(n)), h)
+    return B, n.value
+
+
+def afqmc_det_ratio(h, slice_, site):
+    out = np.empty(2)
+    _check(_lib.afqmc_det_ratio(h, slice_, site, _dptr(out)), h)
+    return out[0], out[1]
+
+
+def afqmc_set_timing(h, enable):
+    _check(_lib.afqmc_set_timing(h, 1 if enable else 0), h)
+
+
+def afqmc_get_timing(h):
+    t = afqmc_timing()
+    _check(_lib.afqmc_get_timing(h, ctypes.byref(t)), h)
+    return {name: (int(t.launches[i]), float(t.ms[i])) for i, name in enumerate(KERNEL_FAMILIES)}
+
+
+def afqmc_last_error(h=None):
+    m = _lib.afqmc_last_error(h)
+    return m.decode() if m else ""
+
+
+def make_params(L, beta, dtau, U, n_delay, n_stab, t=1.0, seed=0, chain=0, measure=0, device=0, L2=None):
+    return afqmc_params(L1=L, L2=L if L2 is None else L2, t=t, U=U, beta=beta, dtau=dtau, theta1=0.0, theta2=0.0,
+                        hs_channel=0, n_delay=n_delay, n_stab=n_stab, precision=0, measure=measure, chain=chain,
+                        device=device, seed=seed)
+
+
+class Chain:
+    """One Markov chain on the GPU (owns an afqmc handle)."""
+
+    def __init__(self, params, stream=None):
+        self.params = params
+        self.h = afqmc_create(params, stream)
+        self.N, self.M, self.Nc = afqmc_dims(self.h)
+
+    def close(self):
+        if self.h:
+            afqmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n=1):
+        return afqmc_sweep(self.h, n)
+
+    def set_field(self, f, sweep_index=0):
+        afqmc_set_field(self.h, f, sweep_index)
+
+    def field(self):
+        return afqmc_get_field(self.h)
+
+    def measure(self):
+        return afqmc_measure(self.h)
+
+    def observables(self):
+        return afqmc_get_obs(self.h)
+
+    def green(self, slice_=0):
+        return afqmc_get_G(self.h, slice_)

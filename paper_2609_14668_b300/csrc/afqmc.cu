@@ -1,0 +1,772 @@
+// libafqmc.so: host orchestration of the DQMC sweep and the C ABI of afqmc.h.
+//
+// Host side: parameter checks, the lattice set-up (Sec. II.A: Bloch function
+// f(k), Eq. h0kMat; the 2x2 propagator blocks of Eq. ExpLambda in closed form),
+// device memory, and the launch schedule of a sweep.  Every step of the Monte
+// Carlo path runs in the kernels of wrap.cuh, update.cuh, linalg.cuh and
+// measure.cuh.
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "afqmc.h"
+#include "common.cuh"
+#include "linalg.cuh"
+#include "measure.cuh"
+#include "update.cuh"
+#include "wrap.cuh"
+
+using namespace afq;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct UDTe {            // U D T of a propagator chain
+    double* Ut = nullptr;  // U stored column-major (row c = column c)
+    double* D = nullptr;
+    double* T = nullptr;   // row-major
+};
+
+struct CudaFail {
+    afqmc_status code;
+    std::string msg;
+};
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            throw CudaFail{AFQMC_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+enum Op { OP_E = 0, OP_EINV = 1, OP_EH = 2, OP_EHINV = 3 };
+
+}  // namespace
+
+struct afqmc_handle {
+    afqmc_params p{};
+    int N = 0, Nc = 0, L1 = 0, L2 = 0, M = 0, ns = 0, nc = 0, nd = 0, W = UPD_WMAX;
+    double gamma = 0.0, egp = 1.0, egm = 1.0;      // e^{gamma}, e^{-gamma}
+    double dl_p = 0.0, dl_m = 0.0, ef_p = 1.0, ef_m = 1.0;
+    uint64_t key = 0, sweep_index = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sms = 0;
+    bool broken = false;
+    std::string err;
+    // device memory
+    std::vector<void*> allocs;
+    int8_t* field = nullptr;
+    double* G = nullptr;
+    double* Wk[6] = {};
+    double *Xs = nullptr, *Ys = nullptr, *mcoef = nullptr, *xw = nullptr, *yw = nullptr, *Gw = nullptr;
+    int *msite = nullptr, *ctl = nullptr, *perm = nullptr;
+    double *vtmp = nullptr, *Dp = nullptr, *sgn = nullptr, *tau = nullptr, *DbR = nullptr, *DsR = nullptr,
+           *DbL = nullptr, *DsL = nullptr;
+    unsigned int* flags = nullptr;
+    unsigned int epoch = 0;
+    double2* blocks = nullptr;     // 4 operators x Nc x 4
+    double2 *tw1 = nullptr, *tw2 = nullptr;
+    DevStatus* st = nullptr;
+    unsigned long long* n_acc = nullptr;
+    unsigned long long* drift = nullptr;
+    double *czz = nullptr, *hab = nullptr;                     // per-measurement scratch
+    double *obs_now = nullptr, *czz_now = nullptr, *nk_now = nullptr;
+    double *obs_acc = nullptr, *czz_acc = nullptr, *nk_acc = nullptr;
+    long long* obs_count = nullptr;
+    std::vector<UDTe> Rst, Lst;
+    UDTe tmpA, tmpB;               // scratch entries for get_G
+    FFTPlan plan{};
+    int vp = 1;
+    size_t rowop_smem = 0;
+    bool qr_smem_cols = false;     // QR keeps each CTA's columns in shared memory
+    // launch accounting and optional per-launch event timing
+    uint64_t launches = 0;
+    bool timing = false;
+    uint64_t cat_launches[AFQMC_K_COUNT] = {};
+    double cat_ms[AFQMC_K_COUNT] = {};
+    std::vector<cudaEvent_t> ev_free;
+    struct Pending { cudaEvent_t a, b; int cat; };
+    std::vector<Pending> pending;
+
+    template <class T>
+    T* dalloc(size_t n) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaMalloc(&ptr, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+        if (e != cudaSuccess) throw CudaFail{AFQMC_E_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+        allocs.push_back(ptr);
+        return static_cast<T*>(ptr);
+    }
+};
+
+namespace {
+
+// ------------------------------------------------------------------ set-up
+void factor_pair(int n, int& a, int& b) {
+    a = 1;
+    for (int d = 2; d * d <= n; ++d)
+        if (n % d == 0) a = d;
+    b = n / a;
+}
+
+// f(k) = -t [1 + e^{i k.(a1-a2)} + e^{-i k.a2}] (below Eq. h0kMat),
+// k = (l1/L1) b1 + (l2/L2) b2 so k.a_alpha = 2 pi l_alpha / L_alpha.
+std::complex<double> bloch_f(double t, int l1, int l2, int L1, int L2) {
+    const double p1 = 2.0 * M_PI * l1 / L1, p2 = 2.0 * M_PI * l2 / L2;
+    const std::complex<double> I(0.0, 1.0);
+    return -t * (1.0 + std::exp(I * (p1 - p2)) + std::exp(-I * p2));
+}
+
+// e^{-c h(k)} = cosh(c|f|) 1 - sinh(c|f|)/|f| h(k),  h = [[0, f], [f*, 0]]  (Eq. ExpLambda)
+void block_exp(std::complex<double> f, double c, double2 out[4]) {
+    const double af = std::abs(f);
+    const double ch = std::cosh(c * af);
+    const std::complex<double> sf = af > 0.0 ? -std::sinh(c * af) / af * f : std::complex<double>(0.0, 0.0);
+    out[0] = make_double2(ch, 0.0);
+    out[1] = make_double2(sf.real(), sf.imag());
+    out[2] = make_double2(sf.real(), -sf.imag());
+    out[3] = make_double2(ch, 0.0);
+}
+
+void set_error(afqmc_handle* h, afqmc_status code, const std::string& msg) {
+    h->err = msg;
+    if (code == AFQMC_E_CUDA || code == AFQMC_E_TIMEOUT || code == AFQMC_E_NUMERIC) h->broken = true;
+}
+
+// ------------------------------------------------------------------ launches
+cudaEvent_t take_event(afqmc_handle* h) {
+    if (!h->ev_free.empty()) { cudaEvent_t e = h->ev_free.back(); h->ev_free.pop_back(); return e; }
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    return e;
+}
+
+void flush_timing(afqmc_handle* h) {
+    if (h->pending.empty()) return;
+    CK(cudaStreamSynchronize(h->stream));
+    for (auto& q : h->pending) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, q.a, q.b));
+        h->cat_ms[q.cat] += ms;
+        h->ev_free.push_back(q.a);
+        h->ev_free.push_back(q.b);
+    }
+    h->pending.clear();
+}
+
+// Counts one kernel launch of family `cat`; brackets it with events when timing.
+struct Scope {
+    afqmc_handle* h;
+    int cat;
+    cudaEvent_t a = nullptr;
+    Scope(afqmc_handle* h_, int c) : h(h_), cat(c) {
+        h->launches += 1;
+        h->cat_launches[c] += 1;
+        if (h->timing) {
+            if (h->pending.size() > 50000) flush_timing(h);
+            a = take_event(h);
+            CK(cudaEventRecord(a, h->stream));
+        }
+    }
+    ~Scope() {
+        if (!a) return;
+        cudaEvent_t b = nullptr;
+        if (!h->ev_free.empty()) { b = h->ev_free.back(); h->ev_free.pop_back(); }
+        else if (cudaEventCreate(&b) != cudaSuccess) { h->ev_free.push_back(a); return; }
+        if (cudaEventRecord(b, h->stream) != cudaSuccess) { h->ev_free.push_back(a); h->ev_free.push_back(b); return; }
+        h->pending.push_back({a, b, cat});
+    }
+};
+void launch_rowop(afqmc_handle* h, const double* in, double* out, int nrows, Op op, DiagScale pre, DiagScale post,
+                  bool transpose) {
+    const int per = 2 * h->vp;
+    const int grid = (nrows + per - 1) / per;
+    Scope sc(h, AFQMC_K_PROPAGATE);
+    k_rowop<<<grid, 256, h->rowop_smem, h->stream>>>(in, out, nrows, h->N, h->N, h->plan,
+                                                     h->blocks + (size_t)op * h->Nc * 4, pre, post,
+                                                     transpose ? 1 : 0, h->vp);
+    CK(cudaGetLastError());
+}
+
+DiagScale no_scale() { return DiagScale{nullptr, 1.0, 1.0}; }
+DiagScale vscale(afqmc_handle* h, int l, int sign) {   // e^{sign gamma s_l}
+    const int8_t* s = h->field + (size_t)(l - 1) * h->N;
+    return sign > 0 ? DiagScale{s, h->egp, h->egm} : DiagScale{s, h->egm, h->egp};
+}
+
+void gemm(afqmc_handle* h, const double* A, int transA, const double* B, int transB, double* C, double alpha,
+          double beta, const double* rs, int rs_inv, const double* cs, int cs_inv) {
+    const int n = h->N;
+    GemmArgs g{A, B, C, n, n, n, n, n, n, transA, transB, alpha, beta, rs, cs, rs_inv, cs_inv};
+    dim3 grid((n + GT - 1) / GT, (n + GT - 1) / GT);
+    Scope sc(h, AFQMC_K_GEMM);
+    k_dgemm<<<grid, 256, 0, h->stream>>>(g);
+    CK(cudaGetLastError());
+}
+
+void qr(afqmc_handle* h, double* At) {
+    const int n = h->N;
+    h->epoch += 1;
+    if (h->epoch == 0) {   // wrapped: clear the flags once
+        CK(cudaMemsetAsync(h->flags, 0, sizeof(unsigned int) * n, h->stream));
+        h->epoch = 1;
+    }
+    QRArgs q{At, h->tau, h->flags, h->epoch, n, h->st};
+    const int grid = std::min(h->sms, n);
+    int in_smem = h->qr_smem_cols ? 1 : 0;
+    const size_t smem = sizeof(double) * (size_t)n * (in_smem ? 1 + (n + grid - 1) / grid : 1);
+    void* args[] = {&q, &in_smem};
+    Scope sc(h, AFQMC_K_QR);
+    CK(cudaLaunchCooperativeKernel((void*)k_qr_cols, grid, 256, args, smem, h->stream));
+}
+
+int warp_grid(int ncols) { return (ncols * 32 + 255) / 256; }
+
+// out = UDT of (chain of slices lo..hi) applied to `in`:
+//   left  (R chain):  B_hi ... B_lo U D T
+//   !left (L chain):  (B_hi ... B_lo)^T U D T
+void udt_extend(afqmc_handle* h, const UDTe& in, const UDTe& out, int lo, int hi, bool left) {
+    const int n = h->N;
+    double* A = h->Wk[0];
+    CK(cudaMemcpyAsync(A, in.Ut, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, h->stream));
+    if (left) {
+        for (int l = lo; l <= hi; ++l) launch_rowop(h, A, A, n, OP_E, no_scale(), vscale(h, l, +1), false);
+    } else {
+        for (int l = hi; l >= lo; --l) launch_rowop(h, A, A, n, OP_E, vscale(h, l, +1), no_scale(), false);
+    }
+    // pre-pivoting by scaled column norms, unpivoted Householder QR of A P
+    double* AP = h->Wk[1];
+    { Scope sc(h, AFQMC_K_QRAUX); k_colnorm_scaled<<<warp_grid(n), 256, 0, h->stream>>>(A, in.D, h->vtmp, n, h->st); }
+    { Scope sc(h, AFQMC_K_QRAUX); k_rank_perm<<<(n + 255) / 256, 256, 0, h->stream>>>(h->vtmp, h->perm, n); }
+    { Scope sc(h, AFQMC_K_QRAUX); k_gather_rows<<<n, 256, 0, h->stream>>>(A, AP, h->perm, in.D, h->Dp, n); }
+    CK(cudaGetLastError());
+    qr(h, AP);
+    double* F = h->Wk[2];
+    { Scope sc(h, AFQMC_K_QRAUX); k_make_F<<<n, 256, 0, h->stream>>>(AP, h->Dp, F, out.D, h->sgn, n, h->st); }
+    { Scope sc(h, AFQMC_K_QRAUX); k_form_q<<<warp_grid(n), 256, 0, h->stream>>>(AP, h->tau, h->sgn, out.Ut, n); }
+    double* Tp = h->Wk[3];
+    { Scope sc(h, AFQMC_K_QRAUX); k_gather_rows<<<n, 256, 0, h->stream>>>(in.T, Tp, h->perm, nullptr, nullptr, n); }
+    CK(cudaGetLastError());
+    gemm(h, F, 0, Tp, 0, out.T, 1.0, 0.0, nullptr, 0, nullptr, 0);
+}
+
+// G = (1 + R L)^-1 with R = U_R D_R T_R, L^T = U_L D_L T_L (Loh-Gubernatis split).
+void form_green(afqmc_handle* h, const UDTe& R, const UDTe& Lt, double* Gout) {
+    const int n = h->N;
+    { Scope sc(h, AFQMC_K_MISC); k_split_scales<<<(n + 255) / 256, 256, 0, h->stream>>>(R.D, h->DbR, h->DsR, n); }
+    { Scope sc(h, AFQMC_K_MISC); k_split_scales<<<(n + 255) / 256, 256, 0, h->stream>>>(Lt.D, h->DbL, h->DsL, n); }
+    CK(cudaGetLastError());
+    double* Mt = h->Wk[0];   // M column-major = M^T row-major
+    gemm(h, Lt.Ut, 0, R.Ut, 1, Mt, 1.0, 0.0, h->DbL, 1, h->DbR, 1);
+    gemm(h, Lt.T, 0, R.T, 1, Mt, 1.0, 1.0, h->DsL, 0, h->DsR, 0);
+    qr(h, Mt);
+    double* Yt = h->Wk[1];   // Y = Db_R^-1 U_R^T, column-major
+    {
+        dim3 b(32, 8), g((n + 31) / 32, (n + 31) / 32);
+        Scope sc(h, AFQMC_K_QRAUX);
+        k_transpose_scale<<<g, b, 0, h->stream>>>(R.Ut, Yt, n, n, h->DbR, 1, nullptr, 0);
+    }
+    { Scope sc(h, AFQMC_K_QRAUX); k_apply_qt<<<warp_grid(n), 256, 0, h->stream>>>(Mt, h->tau, Yt, n, n); }
+    double* Wt = h->Wk[2];
+    { Scope sc(h, AFQMC_K_QRAUX); k_backsolve<<<warp_grid(n), 256, 0, h->stream>>>(Mt, Yt, Wt, n, n, h->DbL, h->st); }
+    CK(cudaGetLastError());
+    gemm(h, Lt.Ut, 1, Wt, 1, Gout, 1.0, 0.0, nullptr, 0, nullptr, 0);
+}
+
+void set_identity(afqmc_handle* h, const UDTe& e) {
+    const int n = h->N;
+    const size_t nn = (size_t)n * n;
+    { Scope sc(h, AFQMC_K_MISC); k_set_identity<<<(unsigned)((nn + 255) / 256), 256, 0, h->stream>>>(e.Ut, n); }
+    { Scope sc(h, AFQMC_K_MISC); k_set_identity<<<(unsigned)((nn + 255) / 256), 256, 0, h->stream>>>(e.T, n); }
+    { Scope sc(h, AFQMC_K_MISC); k_fill<<<(n + 255) / 256, 256, 0, h->stream>>>(e.D, 1.0, n); }
+    CK(cudaGetLastError());
+}
+
+// G <- B_l G B_l^-1 (dir +1) or B_l^-1 G B_l (dir -1), two transposed row passes.
+void wrap(afqmc_handle* h, double* A, int l, int dir) {
+    const int n = h->N;
+    double* T = h->Wk[4];
+    if (dir > 0) {
+        launch_rowop(h, A, T, n, OP_EINV, no_scale(), vscale(h, l, -1), true);
+        launch_rowop(h, T, A, n, OP_E, no_scale(), vscale(h, l, +1), true);
+    } else {
+        launch_rowop(h, A, T, n, OP_E, vscale(h, l, +1), no_scale(), true);
+        launch_rowop(h, T, A, n, OP_EINV, vscale(h, l, -1), no_scale(), true);
+    }
+}
+
+// half step g = e^{-dtau K/2} A e^{+dtau K/2} into out
+void half_step(afqmc_handle* h, const double* A, double* out) {
+    double* T = h->Wk[4];
+    launch_rowop(h, A, T, h->N, OP_EHINV, no_scale(), no_scale(), true);
+    launch_rowop(h, T, out, h->N, OP_EH, no_scale(), no_scale(), true);
+}
+
+void update_slice(afqmc_handle* h, double* G, int l, int pass, uint64_t sweep) {
+    UpdArgs a{};
+    a.G = G; a.N = h->N; a.Xs = h->Xs; a.Ys = h->Ys; a.msite = h->msite; a.mcoef = h->mcoef;
+    a.xw = h->xw; a.yw = h->yw; a.Gw = h->Gw; a.ctl = h->ctl;
+    a.s = h->field + (size_t)(l - 1) * h->N;
+    a.nd = h->nd; a.W = h->W;
+    a.dl_p = h->dl_p; a.dl_m = h->dl_m; a.ef_p = h->ef_p; a.ef_m = h->ef_m;
+    a.key = h->key;
+    a.ctr0 = ((sweep * 2 + (uint64_t)pass) * (uint64_t)h->M + (uint64_t)(l - 1)) * (uint64_t)h->N + 1;
+    a.n_acc = h->n_acc; a.st = h->st;
+    const size_t smem = sizeof(double) * std::max((size_t)h->W * (h->W + 1) + 2 * h->W, (size_t)2 * h->nd * 32);
+    void* args[] = {&a};
+    Scope sc(h, AFQMC_K_UPDATE);
+    CK(cudaLaunchCooperativeKernel((void*)k_update_slice, h->sms, UPD_THREADS, args, smem, h->stream));
+}
+
+void measure(afqmc_handle* h, const double* G, bool accumulate) {
+    double* g = h->Wk[5];
+    half_step(h, G, g);
+    { Scope sc(h, AFQMC_K_MEASURE); k_measure_pairs<<<h->Nc, 128, 0, h->stream>>>(g, h->L1, h->L2, h->czz, h->hab); }
+    CK(cudaGetLastError());
+    if (accumulate) {
+        { Scope sc(h, AFQMC_K_MEASURE); k_measure_nk<<<(h->Nc + 127) / 128, 128, 0, h->stream>>>(h->hab, h->L1, h->L2, h->tw1, h->tw2, h->nk_acc, 1); }
+        { Scope sc(h, AFQMC_K_MEASURE); k_measure_scalars<<<1, 256, 0, h->stream>>>(g, h->czz, h->L1, h->L2, h->p.t, h->p.U, h->tw1, h->obs_acc,
+                                                    h->czz_acc, 1, h->obs_count, h->st); }
+    } else {
+        { Scope sc(h, AFQMC_K_MEASURE); k_measure_nk<<<(h->Nc + 127) / 128, 128, 0, h->stream>>>(h->hab, h->L1, h->L2, h->tw1, h->tw2, h->nk_now, 0); }
+        { Scope sc(h, AFQMC_K_MEASURE); k_measure_scalars<<<1, 256, 0, h->stream>>>(g, h->czz, h->L1, h->L2, h->p.t, h->p.U, h->tw1, h->obs_now,
+                                                    nullptr, 0, nullptr, h->st); }
+        CK(cudaMemcpyAsync(h->czz_now, h->czz, sizeof(double) * h->Nc, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    CK(cudaGetLastError());
+}
+
+// recompute G at a stack boundary, recording the drift from the wrapped G
+void recompute(afqmc_handle* h, int c) {
+    const size_t nn = (size_t)h->N * h->N;
+    double* saved = h->Wk[5];
+    CK(cudaMemcpyAsync(saved, h->G, sizeof(double) * nn, cudaMemcpyDeviceToDevice, h->stream));
+    form_green(h, h->Rst[c], h->Lst[c], h->G);
+    { Scope sc(h, AFQMC_K_MISC); k_maxabsdiff<<<h->sms * 2, 256, 0, h->stream>>>(h->G, saved, nn, h->drift, h->st); }
+    CK(cudaGetLastError());
+    if (h->p.measure) measure(h, h->G, true);
+}
+
+void init_chain(afqmc_handle* h) {
+    set_identity(h, h->Rst[0]);
+    set_identity(h, h->Lst[h->nc]);
+    for (int c = h->nc - 1; c >= 0; --c) udt_extend(h, h->Lst[c + 1], h->Lst[c], c * h->ns + 1, (c + 1) * h->ns, false);
+    form_green(h, h->Rst[0], h->Lst[0], h->G);
+}
+
+afqmc_status check_device(afqmc_handle* h) {
+    CK(cudaStreamSynchronize(h->stream));
+    DevStatus st;
+    CK(cudaMemcpy(&st, h->st, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st.err == DERR_NUMERIC) {
+        set_error(h, AFQMC_E_NUMERIC, "non-finite value in device computation (site code " + std::to_string(st.where) + ")");
+        return AFQMC_E_NUMERIC;
+    }
+    if (st.err == DERR_TIMEOUT) {
+        set_error(h, AFQMC_E_TIMEOUT, "device-side wait timed out (site code " + std::to_string(st.where) + ")");
+        return AFQMC_E_TIMEOUT;
+    }
+    if (st.err != 0) {
+        set_error(h, AFQMC_E_CUDA, "device error " + std::to_string(st.err));
+        return AFQMC_E_CUDA;
+    }
+    return AFQMC_OK;
+}
+
+void sweep_once(afqmc_handle* h) {
+    const int M = h->M, ns = h->ns;
+    for (int l = 1; l <= M; ++l) {
+        wrap(h, h->G, l, +1);
+        update_slice(h, h->G, l, 0, h->sweep_index);
+        if (l % ns == 0) {
+            const int c = l / ns;
+            udt_extend(h, h->Rst[c - 1], h->Rst[c], (c - 1) * ns + 1, c * ns, true);
+            recompute(h, c);
+        }
+    }
+    for (int l = M; l >= 1; --l) {
+        update_slice(h, h->G, l, 1, h->sweep_index);
+        wrap(h, h->G, l, -1);
+        if ((l - 1) % ns == 0) {
+            const int c = (l - 1) / ns;
+            udt_extend(h, h->Lst[c + 1], h->Lst[c], c * ns + 1, (c + 1) * ns, false);
+            recompute(h, c);
+        }
+    }
+    h->sweep_index += 1;
+}
+
+// fresh G at slice l into out (device): R chain in tmpA/tmpB, L chain in the
+// spare last entries of the two stacks (the sweep state is not touched).
+void green_at(afqmc_handle* h, int l, double* out) {
+    const int ns = h->ns;
+    UDTe cur = h->tmpA, nxt = h->tmpB;
+    set_identity(h, cur);
+    for (int lo = 1; lo <= l; lo += ns) {
+        const int hi = std::min(lo + ns - 1, l);
+        udt_extend(h, cur, nxt, lo, hi, true);
+        std::swap(cur, nxt);
+    }
+    UDTe a = h->Rst[h->nc + 1], b = h->Lst[h->nc + 1];
+    set_identity(h, a);
+    for (int hi = h->M; hi > l; hi -= ns) {
+        const int lo = std::max(hi - ns + 1, l + 1);
+        udt_extend(h, a, b, lo, hi, false);
+        std::swap(a, b);
+    }
+    form_green(h, cur, a, out);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle** out) {
+    if (out) *out = nullptr;
+    if (!p || !out) { g_create_error = "null argument"; return AFQMC_E_INVALID; }
+    const afqmc_params P = *p;
+    auto bad = [&](const char* m) { g_create_error = m; return AFQMC_E_INVALID; };
+    if (P.L1 < 1 || P.L2 < 1 || P.L1 > 64 || P.L2 > 64) return bad("L1, L2 must be in [1, 64]");
+    if (!(P.beta > 0) || !(P.dtau > 0)) return bad("beta and dtau must be positive");
+    if (!(P.U >= 0)) return bad("U must be >= 0");
+    if (P.theta1 != 0.0 || P.theta2 != 0.0) return bad("twisted boundaries are not supported in this version");
+    if (P.hs_channel != 0) return bad("only the spin channel (hs_channel = 0) is supported");
+    if (P.precision != 0) return bad("only precision = 0 (FP64) is supported");
+    const double Mr = P.beta / P.dtau;
+    const int M = (int)std::llround(Mr);
+    if (M < 1 || std::fabs(M * P.dtau - P.beta) > 1e-9) return bad("beta must be an integer multiple of dtau");
+    if (P.n_stab < 1 || M % P.n_stab) return bad("n_stab must divide M = beta/dtau");
+    if (P.n_delay < 1 || P.n_delay > 256) return bad("n_delay must be in [1, 256]");
+    auto* h = new afqmc_handle();
+    try {
+        h->p = P;
+        h->L1 = P.L1; h->L2 = P.L2; h->Nc = P.L1 * P.L2; h->N = 2 * h->Nc; h->M = M;
+        h->ns = P.n_stab; h->nc = M / P.n_stab; h->nd = P.n_delay;
+        h->W = std::min(UPD_WMAX, h->N);
+        h->gamma = std::acosh(std::exp(P.dtau * P.U / 2.0));     // Eq. coupling
+        h->egp = std::exp(h->gamma); h->egm = std::exp(-h->gamma);
+        h->dl_p = std::exp(-2.0 * h->gamma) - 1.0;  h->dl_m = std::exp(2.0 * h->gamma) - 1.0;
+        h->ef_p = std::exp(2.0 * h->gamma);         h->ef_m = std::exp(-2.0 * h->gamma);
+        h->key = sm64_mix(P.seed ^ ((uint64_t)(P.chain + 1) * 0xD1B54A32D192ED03ull));
+        CK(cudaSetDevice(P.device));
+        CK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, P.device));
+        if (cuda_stream) h->stream = (cudaStream_t)cuda_stream;
+        else { CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)); h->own_stream = true; }
+        const int N = h->N, Nc = h->Nc;
+        const size_t nn = (size_t)N * N;
+        // FFT plan, twiddles, propagator blocks
+        FFTPlan& pl = h->plan;
+        pl.N = N; pl.Nc = Nc; pl.L1 = h->L1; pl.L2 = h->L2;
+        factor_pair(h->L1, pl.a1, pl.b1);
+        factor_pair(h->L2, pl.a2, pl.b2);
+        std::vector<double2> t1(h->L1), t2(h->L2);
+        for (int m = 0; m < h->L1; ++m) t1[m] = make_double2(std::cos(2 * M_PI * m / h->L1), -std::sin(2 * M_PI * m / h->L1));
+        for (int m = 0; m < h->L2; ++m) t2[m] = make_double2(std::cos(2 * M_PI * m / h->L2), -std::sin(2 * M_PI * m / h->L2));
+        h->tw1 = h->dalloc<double2>(h->L1);
+        h->tw2 = h->dalloc<double2>(h->L2);
+        CK(cudaMemcpy(h->tw1, t1.data(), sizeof(double2) * h->L1, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->tw2, t2.data(), sizeof(double2) * h->L2, cudaMemcpyHostToDevice));
+        pl.tw1 = h->tw1; pl.tw2 = h->tw2;
+        std::vector<double2> blk((size_t)4 * Nc * 4);
+        const double cs[4] = {P.dtau, -P.dtau, 0.5 * P.dtau, -0.5 * P.dtau};   // e^{-c h(k)}
+        for (int op = 0; op < 4; ++op)
+            for (int l2 = 0; l2 < h->L2; ++l2)
+                for (int l1 = 0; l1 < h->L1; ++l1) {
+                    const int q = l1 + h->L1 * l2;
+                    block_exp(bloch_f(P.t, l1, l2, h->L1, h->L2), cs[op], &blk[((size_t)op * Nc + q) * 4]);
+                }
+        h->blocks = h->dalloc<double2>(blk.size());
+        CK(cudaMemcpy(h->blocks, blk.data(), sizeof(double2) * blk.size(), cudaMemcpyHostToDevice));
+        h->vp = std::max(1, std::min(4, (int)(48000 / (sizeof(double2) * 2 * (size_t)N))));
+        h->rowop_smem = sizeof(double2) * 2 * (size_t)h->vp * N;
+        if (h->rowop_smem > 200 * 1024) throw CudaFail{AFQMC_E_INVALID, "lattice too large for the row kernel"};
+        CK(cudaFuncSetAttribute(k_rowop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->rowop_smem));
+        const size_t usmem = sizeof(double) * std::max((size_t)h->W * (h->W + 1) + 2 * h->W, (size_t)2 * h->nd * 32);
+        CK(cudaFuncSetAttribute(k_update_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem));
+        int occ = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_slice, UPD_THREADS, usmem));
+        if (occ < 1) throw CudaFail{AFQMC_E_INVALID, "update kernel does not fit on an SM"};
+        {
+            const int qg = std::min(h->sms, N);
+            const size_t qs = sizeof(double) * (size_t)N * (1 + (N + qg - 1) / qg);
+            h->qr_smem_cols = qs <= 200 * 1024;
+            const size_t qsm = h->qr_smem_cols ? qs : sizeof(double) * N;
+            CK(cudaFuncSetAttribute(k_qr_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_qr_cols, 256, qsm));
+            if (occ < 1) throw CudaFail{AFQMC_E_INVALID, "QR kernel does not fit on an SM"};
+        }
+        // state
+        h->field = h->dalloc<int8_t>((size_t)M * N);
+        h->G = h->dalloc<double>(nn);
+        for (auto& w : h->Wk) w = h->dalloc<double>(nn);
+        h->Xs = h->dalloc<double>((size_t)h->nd * N);
+        h->Ys = h->dalloc<double>((size_t)h->nd * N);
+        h->msite = h->dalloc<int>(h->nd);
+        h->mcoef = h->dalloc<double>(h->nd);
+        h->xw = h->dalloc<double>((size_t)h->nd * h->W);
+        h->yw = h->dalloc<double>((size_t)h->nd * h->W);
+        h->Gw = h->dalloc<double>((size_t)h->W * h->W);
+        h->ctl = h->dalloc<int>(8);
+        h->perm = h->dalloc<int>(N);
+        h->vtmp = h->dalloc<double>(N);
+        h->Dp = h->dalloc<double>(N);
+        h->sgn = h->dalloc<double>(N);
+        h->tau = h->dalloc<double>(N);
+        h->DbR = h->dalloc<double>(N); h->DsR = h->dalloc<double>(N);
+        h->DbL = h->dalloc<double>(N); h->DsL = h->dalloc<double>(N);
+        h->flags = h->dalloc<unsigned int>(N);
+        CK(cudaMemset(h->flags, 0, sizeof(unsigned int) * N));
+        h->st = h->dalloc<DevStatus>(1);
+        CK(cudaMemset(h->st, 0, sizeof(DevStatus)));
+        h->n_acc = h->dalloc<unsigned long long>(1);
+        h->drift = h->dalloc<unsigned long long>(1);
+        h->czz = h->dalloc<double>(Nc);
+        h->hab = h->dalloc<double>((size_t)4 * Nc);
+        h->obs_now = h->dalloc<double>(OBS_SCALARS);
+        h->czz_now = h->dalloc<double>(Nc);
+        h->nk_now = h->dalloc<double>((size_t)8 * Nc);
+        h->obs_acc = h->dalloc<double>(OBS_SCALARS);
+        h->czz_acc = h->dalloc<double>(Nc);
+        h->nk_acc = h->dalloc<double>((size_t)8 * Nc);
+        h->obs_count = h->dalloc<long long>(1);
+        CK(cudaMemset(h->obs_acc, 0, sizeof(double) * OBS_SCALARS));
+        CK(cudaMemset(h->czz_acc, 0, sizeof(double) * Nc));
+        CK(cudaMemset(h->nk_acc, 0, sizeof(double) * 8 * Nc));
+        CK(cudaMemset(h->obs_count, 0, sizeof(long long)));
+        // stacks: nc+1 entries each, plus one spare per stack for green_at
+        h->Rst.resize(h->nc + 2);
+        h->Lst.resize(h->nc + 2);
+        for (auto* st : {&h->Rst, &h->Lst})
+            for (auto& e : *st) { e.Ut = h->dalloc<double>(nn); e.T = h->dalloc<double>(nn); e.D = h->dalloc<double>(N); }
+        for (auto* e : {&h->tmpA, &h->tmpB}) { e->Ut = h->dalloc<double>(nn); e->T = h->dalloc<double>(nn); e->D = h->dalloc<double>(N); }
+        // initial field from the counter-based stream, then stacks and G
+        { Scope sc(h, AFQMC_K_MISC); k_init_field<<<(unsigned)(((size_t)M * N + 255) / 256), 256, 0, h->stream>>>(h->field, M, N, h->key); }
+        CK(cudaGetLastError());
+        init_chain(h);
+        afqmc_status s = check_device(h);
+        if (s != AFQMC_OK) { g_create_error = h->err; afqmc_destroy(h); return s; }
+    } catch (const CudaFail& f) {
+        g_create_error = f.msg;
+        afqmc_destroy(h);
+        return f.code;
+    } catch (const std::exception& e) {
+        g_create_error = e.what();
+        afqmc_destroy(h);
+        return AFQMC_E_NOMEM;
+    }
+    *out = h;
+    return AFQMC_OK;
+}
+
+afqmc_status afqmc_destroy(afqmc_handle* h) {
+    if (!h) return AFQMC_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (auto& q : h->pending) { cudaEventDestroy(q.a); cudaEventDestroy(q.b); }
+    for (auto e : h->ev_free) cudaEventDestroy(e);
+    for (void* ptr : h->allocs) cudaFree(ptr);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return AFQMC_OK;
+}
+
+#define API_BEGIN(h)                                                          \
+    if (!(h)) return AFQMC_E_INVALID;                                         \
+    if ((h)->broken) { (h)->err = "handle unusable after an earlier CUDA, numeric or timeout error"; return AFQMC_E_STATE; } \
+    try {
+#define API_END(h)                                    \
+    } catch (const CudaFail& f) {                     \
+        set_error((h), f.code, f.msg);                \
+        return f.code;                                \
+    } catch (const std::exception& e) {               \
+        set_error((h), AFQMC_E_NOMEM, e.what());      \
+        return AFQMC_E_NOMEM;                         \
+    }
+
+afqmc_status afqmc_set_field(afqmc_handle* h, const int8_t* s, uint64_t sweep_index) {
+    API_BEGIN(h)
+    if (!s) { h->err = "null field"; return AFQMC_E_INVALID; }
+    const size_t len = (size_t)h->M * h->N;
+    for (size_t o = 0; o < len; ++o)
+        if (s[o] != 1 && s[o] != -1) { h->err = "field entries must be +1 or -1"; return AFQMC_E_INVALID; }
+    CK(cudaMemcpyAsync(h->field, s, len, cudaMemcpyHostToDevice, h->stream));
+    h->sweep_index = sweep_index;
+    init_chain(h);
+    return check_device(h);
+    API_END(h)
+}
+
+afqmc_status afqmc_get_field(afqmc_handle* h, int8_t* s) {
+    API_BEGIN(h)
+    if (!s) { h->err = "null field"; return AFQMC_E_INVALID; }
+    CK(cudaMemcpyAsync(s, h->field, (size_t)h->M * h->N, cudaMemcpyDeviceToHost, h->stream));
+    return check_device(h);
+    API_END(h)
+}
+
+afqmc_status afqmc_sweep(afqmc_handle* h, int32_t n_sweeps, afqmc_sweep_stats* stats) {
+    API_BEGIN(h)
+    if (n_sweeps < 0) { h->err = "n_sweeps < 0"; return AFQMC_E_INVALID; }
+    CK(cudaMemsetAsync(h->n_acc, 0, sizeof(unsigned long long), h->stream));
+    CK(cudaMemsetAsync(h->drift, 0, sizeof(unsigned long long), h->stream));
+    const uint64_t l0 = h->launches;
+    for (int w = 0; w < n_sweeps; ++w) sweep_once(h);
+    if (stats) {
+        unsigned long long acc = 0, dr = 0;
+        CK(cudaMemcpyAsync(&acc, h->n_acc, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(&dr, h->drift, sizeof(dr), cudaMemcpyDeviceToHost, h->stream));
+        afqmc_status s = check_device(h);
+        stats->proposed = (uint64_t)n_sweeps * 2ull * (uint64_t)h->N * (uint64_t)h->M;
+        stats->accepted = acc;
+        double d;
+        std::memcpy(&d, &dr, sizeof(d));
+        stats->max_stab_drift = d;
+        stats->launches = h->launches - l0;
+        return s;
+    }
+    return check_device(h);
+    API_END(h)
+}
+
+static void fill_obs(const double* v, long long n, afqmc_obs* out) {
+    out->energy = v[0]; out->double_occ = v[1]; out->ekin = v[2]; out->density = v[3];
+    out->m2 = v[4]; out->S_af = v[5]; out->S_af_dk = v[6]; out->R_m2 = v[7]; out->Czz_half = v[8];
+    out->n_samples = n;
+}
+
+afqmc_status afqmc_measure(afqmc_handle* h, afqmc_obs* out, double* Czz, double* nk) {
+    API_BEGIN(h)
+    if (!out) { h->err = "null output"; return AFQMC_E_INVALID; }
+    measure(h, h->G, false);
+    double v[OBS_SCALARS];
+    CK(cudaMemcpyAsync(v, h->obs_now, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+    if (Czz) CK(cudaMemcpyAsync(Czz, h->czz_now, sizeof(double) * h->Nc, cudaMemcpyDeviceToHost, h->stream));
+    if (nk) CK(cudaMemcpyAsync(nk, h->nk_now, sizeof(double) * 8 * h->Nc, cudaMemcpyDeviceToHost, h->stream));
+    afqmc_status s = check_device(h);
+    fill_obs(v, 1, out);
+    return s;
+    API_END(h)
+}
+
+afqmc_status afqmc_get_obs(afqmc_handle* h, afqmc_obs* out, double* Czz, double* nk) {
+    API_BEGIN(h)
+    if (!out) { h->err = "null output"; return AFQMC_E_INVALID; }
+    double v[OBS_SCALARS];
+    long long n = 0;
+    std::vector<double> cz(h->Nc), nkv((size_t)8 * h->Nc);
+    CK(cudaMemcpyAsync(v, h->obs_acc, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&n, h->obs_count, sizeof(n), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(cz.data(), h->czz_acc, sizeof(double) * h->Nc, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(nkv.data(), h->nk_acc, sizeof(double) * 8 * h->Nc, cudaMemcpyDeviceToHost, h->stream));
+    afqmc_status s = check_device(h);
+    if (s != AFQMC_OK) return s;
+    const double inv = n > 0 ? 1.0 / (double)n : 0.0;
+    for (double& x : v) x *= inv;
+    fill_obs(v, n, out);
+    if (Czz) for (int d = 0; d < h->Nc; ++d) Czz[d] = cz[d] * inv;
+    if (nk) for (size_t q = 0; q < nkv.size(); ++q) nk[q] = nkv[q] * inv;
+    CK(cudaMemsetAsync(h->obs_acc, 0, sizeof(double) * OBS_SCALARS, h->stream));
+    CK(cudaMemsetAsync(h->czz_acc, 0, sizeof(double) * h->Nc, h->stream));
+    CK(cudaMemsetAsync(h->nk_acc, 0, sizeof(double) * 8 * h->Nc, h->stream));
+    CK(cudaMemsetAsync(h->obs_count, 0, sizeof(long long), h->stream));
+    return check_device(h);
+    API_END(h)
+}
+
+afqmc_status afqmc_get_G(afqmc_handle* h, int32_t slice, double* out) {
+    API_BEGIN(h)
+    if (!out || slice < 0 || slice > h->M) { h->err = "bad slice or null output"; return AFQMC_E_INVALID; }
+    double* dst = h->Wk[5];
+    green_at(h, slice, dst);
+    CK(cudaMemcpyAsync(out, dst, sizeof(double) * h->N * h->N, cudaMemcpyDeviceToHost, h->stream));
+    return check_device(h);
+    API_END(h)
+}
+
+afqmc_status afqmc_wrap_matrix(afqmc_handle* h, int32_t slice, int32_t direction, double* A) {
+    API_BEGIN(h)
+    if (!A || slice < 1 || slice > h->M || direction < -1 || direction > 1) { h->err = "bad arguments"; return AFQMC_E_INVALID; }
+    double* d = h->Wk[3];
+    const size_t bytes = sizeof(double) * h->N * h->N;
+    CK(cudaMemcpyAsync(d, A, bytes, cudaMemcpyHostToDevice, h->stream));
+    if (direction == 0) {
+        half_step(h, d, h->Wk[5]);
+        CK(cudaMemcpyAsync(A, h->Wk[5], bytes, cudaMemcpyDeviceToHost, h->stream));
+    } else {
+        wrap(h, d, slice, direction);
+        CK(cudaMemcpyAsync(A, d, bytes, cudaMemcpyDeviceToHost, h->stream));
+    }
+    return check_device(h);
+    API_END(h)
+}
+
+afqmc_status afqmc_update_slice(afqmc_handle* h, int32_t slice, int32_t pass, uint64_t sweep_index, double* G,
+                                int32_t* n_accepted) {
+    API_BEGIN(h)
+    if (!G || slice < 1 || slice > h->M || (pass != 0 && pass != 1)) { h->err = "bad arguments"; return AFQMC_E_INVALID; }
+    double* d = h->Wk[5];
+    const size_t bytes = sizeof(double) * h->N * h->N;
+    CK(cudaMemcpyAsync(d, G, bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(h->n_acc, 0, sizeof(unsigned long long), h->stream));
+    update_slice(h, d, slice, pass, sweep_index);
+    unsigned long long acc = 0;
+    CK(cudaMemcpyAsync(G, d, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&acc, h->n_acc, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
+    afqmc_status s = check_device(h);
+    if (n_accepted) *n_accepted = (int32_t)acc;
+    return s;
+    API_END(h)
+}
+
+afqmc_status afqmc_det_ratio(afqmc_handle* h, int32_t slice, int32_t site, double out[2]) {
+    API_BEGIN(h)
+    if (!out || slice < 1 || slice > h->M || site < 0 || site >= h->N) { h->err = "bad arguments"; return AFQMC_E_INVALID; }
+    double* g = h->Wk[5];
+    green_at(h, slice, g);
+    int8_t sv = 0;
+    CK(cudaMemcpyAsync(&sv, h->field + (size_t)(slice - 1) * h->N + site, 1, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    double* o = h->vtmp;
+    { Scope sc(h, AFQMC_K_MISC); k_ratio<<<1, 1, 0, h->stream>>>(g, h->N, site, sv, h->dl_p, h->dl_m, h->ef_p, h->ef_m, o); }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, o, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return check_device(h);
+    API_END(h)
+}
+
+afqmc_status afqmc_set_timing(afqmc_handle* h, int32_t enable) {
+    API_BEGIN(h)
+    flush_timing(h);
+    h->timing = enable != 0;
+    for (int c = 0; c < AFQMC_K_COUNT; ++c) { h->cat_launches[c] = 0; h->cat_ms[c] = 0.0; }
+    return AFQMC_OK;
+    API_END(h)
+}
+
+afqmc_status afqmc_get_timing(afqmc_handle* h, afqmc_timing* out) {
+    API_BEGIN(h)
+    if (!out) { h->err = "null output"; return AFQMC_E_INVALID; }
+    flush_timing(h);
+    for (int c = 0; c < AFQMC_K_COUNT; ++c) { out->launches[c] = h->cat_launches[c]; out->ms[c] = h->cat_ms[c]; }
+    return check_device(h);
+    API_END(h)
+}
+
+afqmc_status afqmc_dims(const afqmc_handle* h, int32_t* N, int32_t* M, int32_t* Nc) {
+    if (!h) return AFQMC_E_INVALID;
+    if (N) *N = h->N;
+    if (M) *M = h->M;
+    if (Nc) *Nc = h->Nc;
+    return AFQMC_OK;
+}
+
+const char* afqmc_last_error(const afqmc_handle* h) {
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Shared device helpers: counter-based random numbers, bounded grid barrier,
+// global-timer timeouts, small reductions.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace afq {
+
+// Error codes written into DevStatus::err by device code (mirrors afqmc_status).
+enum : int { DERR_OK = 0, DERR_NUMERIC = 4, DERR_TIMEOUT = 5 };
+
+// Wall-clock limit of any single device-side wait (nanoseconds).
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
+
+struct DevStatus {
+    int err;            // first error seen (0 = none)
+    int where;          // code of the wait that timed out
+    unsigned int bar_count, bar_gen;   // grid barrier state
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): n-th output of the stream with seed k
+// is mix(k + n*0x9E3779B97F4A7C15); finaliser constants of the published generator.
+__host__ __device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ double sm64_uniform(uint64_t key, uint64_t n) {
+    return (double)(sm64_mix(key + n * 0x9E3779B97F4A7C15ull) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// Grid-wide barrier for cooperative launches.  Every CTA must call it.  The
+// wait is bounded by WAIT_LIMIT_NS; on timeout the error flag is set and the
+// function returns false, as it does when any CTA has flagged an error.
+__device__ __forceinline__ bool grid_barrier(DevStatus* st, int where) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* vgen = &st->bar_gen;
+        unsigned int gen = *vgen;
+        __threadfence();
+        unsigned int arrived = atomicAdd(&st->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            st->bar_count = 0;
+            __threadfence();
+            atomicAdd(&st->bar_gen, 1u);
+        } else {
+            unsigned long long t0 = global_ns();
+            while (*vgen == gen) {
+                if (*(volatile int*)&st->err) break;
+                if (global_ns() - t0 > WAIT_LIMIT_NS) {
+                    if (atomicCAS(&st->err, 0, DERR_TIMEOUT) == 0) st->where = where;
+                    break;
+                }
+                __nanosleep(20);
+            }
+        }
+        __threadfence();
+        s_ok = (*(volatile int*)&st->err) == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ void flag_error(DevStatus* st, int code, int where) {
+    if (atomicCAS(&st->err, 0, code) == 0) st->where = where;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum (blockDim.x a multiple of 32, <= 1024); result valid in all threads.
+__device__ __forceinline__ double block_sum(double v, double* scratch /* >= 33 doubles */) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) scratch[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        double x = lane < nw ? scratch[lane] : 0.0;
+        x = warp_sum(x);
+        if (lane == 0) scratch[32] = x;
+    }
+    __syncthreads();
+    return scratch[32];
+}
+
+}  // namespace afq

@@ -1,0 +1,402 @@
+// FP64 dense linear algebra for the QR stabilisation of Sec. II.B ('Second')
+// and the recomputation of G = (1 + R L)^-1 (Eq. GrFMat).
+//
+// B300 design notes.  FP64 runs at ~1.1 TFLOP/s on this part (SIMT DFMA is a
+// little faster than the FP64 tensor path, DMMA), so every kernel here is
+// bound by the FP64 pipes, not by memory: the working matrices (10.6 MB at
+// N = 1152) stay resident in the 126 MB L2.  The kernels therefore aim at
+// keeping all 148 SMs' FP64 units busy:
+//   * k_dgemm: 64x64 register-tiled SIMT GEMM with row/column scaling epilogue;
+//   * k_qr_cols: Householder QR as one cooperative kernel, columns owned
+//     cyclically by CTAs, reflector j published through a flag and applied by
+//     every CTA to its own columns (one-column lookahead on the critical path);
+//   * column-parallel kernels (one warp per column, no inter-CTA sync) for
+//     applying the reflectors, forming Q and back substitution.
+// Matrices are row-major; a "column-major" matrix X is stored as its
+// transpose Xt (row c of Xt = column c of X).
+#pragma once
+#include "common.cuh"
+
+namespace afq {
+
+// C[i][j] = alpha * rs_i * (op(A) op(B))_ij * cs_j + beta * C[i][j]
+// op(A) is m x k: A[i][p] (transA = 0, lda >= k) or A[p][i] (transA = 1, lda >= m).
+// op(B) is k x n: B[p][j] (transB = 0) or B[j][p] (transB = 1).
+struct GemmArgs {
+    const double* A; const double* B; double* C;
+    int m, n, k, lda, ldb, ldc, transA, transB;
+    double alpha, beta;
+    const double* rs; const double* cs;   // optional (nullptr = 1)
+    int rs_inv, cs_inv;                   // 1: scale by the reciprocal
+};
+
+// 32 x 32 output tiles (1296 CTAs at N = 1152: 8.8 per SM, so the last wave is
+// nearly full), 256 threads with 2 x 2 outputs each.  FP64 FMAs, not shared
+// memory or L2 bandwidth, are the limit at this size.
+constexpr int GT = 32, GK = 32;
+
+__global__ void __launch_bounds__(256) k_dgemm(GemmArgs g) {
+    __shared__ double As[GK][GT + 1];
+    __shared__ double Bs[GK][GT + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    for (int p0 = 0; p0 < g.k; p0 += GK) {
+        for (int o = threadIdx.x; o < GK * GT; o += 256) {
+            int pp, ii;
+            if (g.transA) { pp = o / GT; ii = o % GT; } else { ii = o / GK; pp = o % GK; }
+            const int gi = i0 + ii, gp = p0 + pp;
+            double v = 0.0;
+            if (gi < g.m && gp < g.k) v = g.transA ? g.A[(size_t)gp * g.lda + gi] : g.A[(size_t)gi * g.lda + gp];
+            As[pp][ii] = v;
+            int jj;
+            if (g.transB) { jj = o / GK; pp = o % GK; } else { pp = o / GT; jj = o % GT; }
+            const int gj = j0 + jj, gq = p0 + pp;
+            double w = 0.0;
+            if (gj < g.n && gq < g.k) w = g.transB ? g.B[(size_t)gj * g.ldb + gq] : g.B[(size_t)gq * g.ldb + gj];
+            Bs[pp][jj] = w;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int p = 0; p < GK; ++p) {
+            const double a0 = As[p][ty], a1 = As[p][ty + 16];
+            const double b0 = Bs[p][tx], b1 = Bs[p][tx + 16];
+            acc[0][0] = fma(a0, b0, acc[0][0]);
+            acc[0][1] = fma(a0, b1, acc[0][1]);
+            acc[1][0] = fma(a1, b0, acc[1][0]);
+            acc[1][1] = fma(a1, b1, acc[1][1]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const int i = i0 + ty + 16 * a;
+        if (i >= g.m) continue;
+        double r = g.alpha;
+        if (g.rs) r = g.rs_inv ? r / g.rs[i] : r * g.rs[i];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int j = j0 + tx + 16 * b;
+            if (j >= g.n) continue;
+            double v = acc[a][b] * r;
+            if (g.cs) v = g.cs_inv ? v / g.cs[j] : v * g.cs[j];
+            double* c = g.C + (size_t)i * g.ldc + j;
+            *c = (g.beta == 0.0) ? v : fma(g.beta, *c, v);
+        }
+    }
+}
+
+// out[j][i] = in[i][j] * (rs ? rs[i] : 1) * (cs ? cs[j] : 1)   (in: m x n, row-major)
+__global__ void k_transpose_scale(const double* __restrict__ in, double* __restrict__ out, int m, int n,
+                                  const double* rs, int rs_inv, const double* cs, int cs_inv) {
+    __shared__ double tile[32][33];
+    const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int i = bi + y, j = bj + threadIdx.x;
+        double v = 0.0;
+        if (i < m && j < n) {
+            v = in[(size_t)i * n + j];
+            if (rs) v = rs_inv ? v / rs[i] : v * rs[i];
+            if (cs) v = cs_inv ? v / cs[j] : v * cs[j];
+        }
+        tile[y][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int j = bj + y, i = bi + threadIdx.x;
+        if (i < m && j < n) out[(size_t)j * m + i] = tile[threadIdx.x][y];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR of a column-major n x n matrix A (array At, row c = column c).
+// On exit: R in the upper triangle (At[c][i], i <= c), reflector j stored below
+// the diagonal (At[j][i], i > j, implicit 1 at i = j), tau[j].
+// H_j = I - tau_j v_j v_j^T,  A = H_0 H_1 ... H_{n-2} R.
+// Cooperative launch; column c is owned by CTA c % gridDim.x.  flags[j] is set
+// to `epoch` once reflector j is final.
+// ---------------------------------------------------------------------------
+struct QRArgs {
+    double* At; double* tau; unsigned int* flags; unsigned int epoch; int n;
+    DevStatus* st;
+};
+
+// Publish column j (final: R entries above the diagonal, beta on it, the
+// reflector below) to global memory and raise flags[j].
+__device__ void qr_publish(const QRArgs& q, const double* col, int j, bool copy) {
+    double* g = q.At + (size_t)j * q.n;
+    if (copy)
+        for (int i = threadIdx.x; i < q.n; i += blockDim.x) g[i] = col[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(&q.flags[j], q.epoch);
+    }
+}
+
+// Householder reflector of column j (rows j..n-1), in place in `col`; whole CTA.
+__device__ void qr_make_reflector(const QRArgs& q, double* col, int j, double* red) {
+    const int n = q.n;
+    double s = 0.0;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) { const double x = col[i]; s = fma(x, x, s); }
+    s = block_sum(s, red);
+    const double alpha = col[j];
+    double tau = 0.0, beta = alpha, scale = 0.0;
+    if (s > 0.0) {
+        const double nrm = sqrt(fma(alpha, alpha, s));
+        beta = alpha <= 0.0 ? nrm : -nrm;
+        tau = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+    }
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) col[i] *= scale;
+    if (threadIdx.x == 0) {
+        col[j] = beta;
+        q.tau[j] = tau;
+        if (!isfinite(beta) || !isfinite(tau)) flag_error(q.st, DERR_NUMERIC, 100);
+    }
+    __syncthreads();
+}
+
+// Apply H_j (v in shared memory, rows j..n-1, v[0] = 1) to a column; one warp.
+__device__ __forceinline__ void qr_apply_warp(const double* __restrict__ v, double tau, double* col, int j, int n) {
+    const int lane = threadIdx.x & 31;
+    double w = 0.0;
+    for (int i = j + lane; i < n; i += 32) w = fma(v[i - j], col[i], w);
+    w = warp_sum(w) * tau;
+    for (int i = j + lane; i < n; i += 32) col[i] = fma(-w, v[i - j], col[i]);
+}
+
+// Apply H_j to a column with the whole CTA (the lookahead column on the critical path).
+__device__ void qr_apply_block(const double* __restrict__ v, double tau, double* col, int j, int n, double* red) {
+    double w = 0.0;
+    for (int i = j + threadIdx.x; i < n; i += blockDim.x) w = fma(v[i - j], col[i], w);
+    w = block_sum(w, red) * tau;
+    for (int i = j + threadIdx.x; i < n; i += blockDim.x) col[i] = fma(-w, v[i - j], col[i]);
+    __syncthreads();
+}
+
+// Dynamic shared memory: n doubles for the current reflector, plus (when
+// cols_in_smem) ceil(n / gridDim.x) * n doubles holding this CTA's columns.
+__global__ void __launch_bounds__(256) k_qr_cols(QRArgs q, int cols_in_smem) {
+    extern __shared__ double qr_smem[];
+    __shared__ double red[33];
+    __shared__ int s_abort;
+    const int n = q.n, G = gridDim.x, me = blockIdx.x;
+    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    double* v = qr_smem;
+    double* cols = qr_smem + n;
+    auto col = [&](int c) -> double* {
+        return cols_in_smem ? cols + (size_t)((c - me) / G) * n : q.At + (size_t)c * n;
+    };
+    if (threadIdx.x == 0) s_abort = 0;
+    if (cols_in_smem)
+        for (int c = me; c < n; c += G) {
+            double* d = col(c);
+            for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = q.At[(size_t)c * n + i];
+        }
+    __syncthreads();
+    if (me == 0) {
+        qr_make_reflector(q, col(0), 0, red);
+        qr_publish(q, col(0), 0, cols_in_smem);
+    }
+    for (int j = 0; j < n - 1; ++j) {
+        if (threadIdx.x == 0) {
+            volatile unsigned int* f = q.flags + j;
+            unsigned long long t0 = global_ns();
+            while (*f != q.epoch) {
+                if (*(volatile int*)&q.st->err) { s_abort = 1; break; }
+                if (global_ns() - t0 > WAIT_LIMIT_NS) { flag_error(q.st, DERR_TIMEOUT, 101); s_abort = 1; break; }
+                __nanosleep(20);
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        if (s_abort) return;
+        const double* colj = q.At + (size_t)j * n;
+        for (int i = j + threadIdx.x; i < n; i += blockDim.x) v[i - j] = (i == j) ? 1.0 : __ldcg(colj + i);
+        const double tau = __ldcg(q.tau + j);
+        __syncthreads();
+        // lookahead: the owner of column j+1 finishes it first and publishes it
+        if ((j + 1) % G == me) {
+            double* c1 = col(j + 1);
+            if (tau != 0.0) qr_apply_block(v, tau, c1, j, n, red);
+            if (j + 1 < n - 1) qr_make_reflector(q, c1, j + 1, red);
+            qr_publish(q, c1, j + 1, cols_in_smem);
+        }
+        if (tau != 0.0) {
+            int cnt = 0;
+            for (int c = j + 2 + ((me - (j + 2)) % G + G) % G; c < n; c += G, ++cnt)
+                if (cnt % nwarp == warp) qr_apply_warp(v, tau, col(c), j, n);
+        }
+        __syncthreads();
+    }
+}
+
+// Apply Q^T = H_{n-2} ... H_0 to every column of Y (Yt row-major, ncols columns
+// of length n), i.e. H_0 first.  One warp per column.
+__global__ void __launch_bounds__(256) k_apply_qt(const double* __restrict__ Vt, const double* __restrict__ tau,
+                                                  double* Yt, int n, int ncols) {
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= ncols) return;
+    double* y = Yt + (size_t)gw * n;
+    for (int j = 0; j < n - 1; ++j) {
+        const double tj = __ldg(tau + j);
+        if (tj == 0.0) continue;
+        const double* vj = Vt + (size_t)j * n;
+        double w = lane == 0 ? y[j] : 0.0;
+        for (int i = j + 1 + lane; i < n; i += 32) w = fma(__ldg(vj + i), y[i], w);
+        w = warp_sum(w) * tj;
+        if (lane == 0) y[j] -= w;
+        for (int i = j + 1 + lane; i < n; i += 32) y[i] = fma(-w, __ldg(vj + i), y[i]);
+        __syncwarp();
+    }
+}
+
+// Form column c of Q = H_0 ... H_{n-2} (Qt row c), multiplied by sgn[c]:
+// start from e_c, apply H_j for j = min(c, n-2) down to 0.  One warp per column.
+__global__ void __launch_bounds__(256) k_form_q(const double* __restrict__ Vt, const double* __restrict__ tau,
+                                                const double* __restrict__ sgn, double* Qt, int n) {
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= n) return;
+    double* q = Qt + (size_t)c * n;
+    for (int i = lane; i < n; i += 32) q[i] = (i == c) ? 1.0 : 0.0;
+    __syncwarp();
+    for (int j = min(c, n - 2); j >= 0; --j) {
+        const double tj = __ldg(tau + j);
+        if (tj == 0.0) continue;
+        const double* vj = Vt + (size_t)j * n;
+        double w = lane == 0 ? q[j] : 0.0;
+        for (int i = j + 1 + lane; i < n; i += 32) w = fma(__ldg(vj + i), q[i], w);
+        w = warp_sum(w) * tj;
+        if (lane == 0) q[j] -= w;
+        for (int i = j + 1 + lane; i < n; i += 32) q[i] = fma(-w, __ldg(vj + i), q[i]);
+        __syncwarp();
+    }
+    const double s = sgn[c];
+    for (int i = lane; i < n; i += 32) q[i] *= s;
+}
+
+// Back substitution: for every column y (row of Yt), solve R x = y with R the
+// upper triangle of the column-major Rt (R[i][c] = Rt[c][i]); writes
+// x_i * (xs ? 1/xs[i] : 1) into Xt.  One warp per column.
+__global__ void __launch_bounds__(256) k_backsolve(const double* __restrict__ Rt, const double* __restrict__ Yt,
+                                                   double* Xt, int n, int ncols, const double* xs, DevStatus* st) {
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= ncols) return;
+    const double* y = Yt + (size_t)c * n;
+    double* x = Xt + (size_t)c * n;
+    for (int i = lane; i < n; i += 32) x[i] = y[i];
+    __syncwarp();
+    for (int i = n - 1; i >= 0; --i) {
+        const double* ri = Rt + (size_t)i * n;
+        const double xi = x[i] / __ldg(ri + i);
+        __syncwarp();
+        if (lane == 0) x[i] = xi;
+        for (int r = lane; r < i; r += 32) x[r] = fma(-__ldg(ri + r), xi, x[r]);
+        __syncwarp();
+    }
+    bool bad = false;
+    for (int i = lane; i < n; i += 32) {
+        double v = x[i];
+        if (xs) v /= xs[i];
+        if (!isfinite(v)) bad = true;
+        x[i] = v;
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) flag_error(st, DERR_NUMERIC, 102);
+}
+
+// Column norms w_c = D_c * ||A_c|| of a column-major A (At); one warp per column.
+__global__ void k_colnorm_scaled(const double* __restrict__ At, const double* __restrict__ D, double* w, int n,
+                                 DevStatus* st) {
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= n) return;
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) { const double x = At[(size_t)c * n + i]; s = fma(x, x, s); }
+    s = warp_sum(s);
+    if (lane == 0) {
+        double v = sqrt(s) * D[c];
+        if (!isfinite(v)) { flag_error(st, DERR_NUMERIC, 105); v = 0.0; }   // keeps the ranks a permutation
+        w[c] = v;
+    }
+}
+
+// Pre-pivoting (Bai, Lee, Li & Xu 2011): permutation sorting columns by w,
+// descending, ties by index.  perm[rank] = c.
+__global__ void k_rank_perm(const double* __restrict__ w, int* perm, int n) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const double wc = w[c];
+    int rank = 0;
+    for (int d = 0; d < n; ++d) {
+        const double wd = w[d];
+        rank += (wd > wc) || (wd == wc && d < c);
+    }
+    perm[rank] = c;
+}
+
+// Row gather: out[k][:] = in[perm[k]][:], and Dp[k] = D[perm[k]].
+__global__ void k_gather_rows(const double* __restrict__ in, double* out, const int* __restrict__ perm,
+                              const double* __restrict__ D, double* Dp, int n) {
+    const int k = blockIdx.x;
+    int src = perm[k];
+    if (src < 0 || src >= n) src = k;   // defensive: perm is always a permutation of [0, n)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) out[(size_t)k * n + i] = in[(size_t)src * n + i];
+    if (threadIdx.x == 0 && D) Dp[k] = D[src];
+}
+
+// From the QR of A P (R in the column-major Rt) and the permuted scales Dp:
+// Dnew_i = |R_ii| Dp_i, sgn_i = sign(R_ii), F = Dnew^-1 S R Dp (unit upper
+// triangular, row-major), so that (A D) P = (Q S) Dnew F.
+__global__ void k_make_F(const double* __restrict__ Rt, const double* __restrict__ Dp, double* F,
+                         double* Dnew, double* sgn, int n, DevStatus* st) {
+    const int i = blockIdx.x;
+    const double rii = Rt[(size_t)i * n + i];
+    const double s = rii < 0.0 ? -1.0 : 1.0;
+    const double dn = fabs(rii) * Dp[i];
+    if (threadIdx.x == 0) {
+        Dnew[i] = dn;
+        sgn[i] = s;
+        if (!(dn > 0.0) || !isfinite(dn)) flag_error(st, DERR_NUMERIC, 103);
+    }
+    const double f = s / dn;
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+        F[(size_t)i * n + j] = (j < i) ? 0.0 : (j == i ? 1.0 : Rt[(size_t)j * n + i] * Dp[j] * f);
+}
+
+// M = Db_R^-1 P1 Db_L^-1 + Ds_R P2 Ds_L is built by two GEMMs; these helpers
+// split D into Db = max(D,1), Ds = min(D,1).
+__global__ void k_split_scales(const double* __restrict__ D, double* Db, double* Ds, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) { const double d = D[i]; Db[i] = fmax(d, 1.0); Ds[i] = fmin(d, 1.0); }
+}
+
+__global__ void k_set_identity(double* A, int n) {
+    const size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o < (size_t)n * n) A[o] = (o / n == o % n) ? 1.0 : 0.0;
+}
+
+__global__ void k_fill(double* a, double v, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+
+// max |A - B| (elementwise) and NaN detection -> out[0] (atomic max on the bit pattern of a non-negative double).
+__global__ void k_maxabsdiff(const double* __restrict__ A, const double* __restrict__ B, size_t len,
+                             unsigned long long* out, DevStatus* st) {
+    double m = 0.0;
+    bool bad = false;
+    for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < len; o += (size_t)gridDim.x * blockDim.x) {
+        const double d = fabs(A[o] - B[o]);
+        if (!isfinite(A[o])) bad = true;
+        m = fmax(m, d);
+    }
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) flag_error(st, DERR_NUMERIC, 104);
+}
+
+}  // namespace afq

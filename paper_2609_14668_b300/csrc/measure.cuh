@@ -1,0 +1,151 @@
+// Equal-time observables by Wick contraction (Sec. II.C; App. C) on the
+// symmetric-split Green's function g = e^{-dtau K/2} G e^{+dtau K/2} of the spin
+// up channel (real path).  With the partial particle-hole transform,
+// G_dn_ij = (-1)^{i+j} (delta_ij - g_ji), which gives for the real path:
+//   n_i_up = 1 - g_ii,  n_i_dn = g_ii,  <n_i_up n_i_dn> = (1 - g_ii) g_ii,
+//   <s_i s_j> = 1/4 [ m_i m_j + 2 g_ij (delta_ij - g_ji) ]  (i, j on one sublattice),
+//   m_i = 1 - 2 g_ii,  <H0> = 2t sum_bonds (g_AB + g_BA).
+#pragma once
+#include "common.cuh"
+
+namespace afq {
+
+constexpr int OBS_SCALARS = 9;   // energy, D, ekin, density, m2, S_af, S_af_dk, R_m2, Czz_half
+
+// One CTA per Bravais displacement d = d1 + L1*d2:
+//   czz[d]  = (1 / 2Nc) sum_{sub, I} <s_{sub,I} s_{sub,I+d}>
+//   h[4d + 2a + b] = sum_J <a^+_{J+d} b_J>  with <c_i^+ c_j> = delta_ij - g_ji
+__global__ void k_measure_pairs(const double* __restrict__ g, int L1, int L2, double* czz, double* h) {
+    __shared__ double red[33];
+    const int Nc = L1 * L2, N = 2 * Nc;
+    const int d = blockIdx.x;
+    const int d1 = d % L1, d2 = d / L1;
+    double acc_s = 0.0, hab[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int I = threadIdx.x; I < Nc; I += blockDim.x) {
+        const int n1 = I % L1, n2 = I / L1;
+        const int J = ((n1 + d1) % L1) + L1 * ((n2 + d2) % L2);     // I + d
+        for (int sub = 0; sub < 2; ++sub) {
+            const int i = sub * Nc + I, j = sub * Nc + J;
+            const double gii = g[(size_t)i * N + i], gjj = g[(size_t)j * N + j];
+            const double gij = g[(size_t)i * N + j], gji = g[(size_t)j * N + i];
+            acc_s += 0.25 * ((1.0 - 2.0 * gii) * (1.0 - 2.0 * gjj) + 2.0 * gij * ((i == j ? 1.0 : 0.0) - gji));
+        }
+        // <a^+_{K+d} b_K> summed over K: here K = I, K+d = J
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                const int ia = a * Nc + J, jb = b * Nc + I;
+                hab[2 * a + b] += (ia == jb ? 1.0 : 0.0) - g[(size_t)jb * N + ia];
+            }
+    }
+    acc_s = block_sum(acc_s, red);
+    if (threadIdx.x == 0) czz[d] = acc_s / (2.0 * Nc);
+    for (int q = 0; q < 4; ++q) {
+        const double v = block_sum(hab[q], red);
+        if (threadIdx.x == 0) h[4 * d + q] = v;
+    }
+}
+
+// n_ab(k) = Nc^-1 sum_d e^{i k.d} h_ab(d) (Eq. nkMatrix); one thread per k.
+// tw1[m] = e^{-2 pi i m/L1}, tw2[m] = e^{-2 pi i m/L2}.  nk: interleaved complex,
+// index (k*4 + 2a + b).  acc != 0 adds into nk.
+__global__ void k_measure_nk(const double* __restrict__ h, int L1, int L2, const double2* __restrict__ tw1,
+                             const double2* __restrict__ tw2, double* nk, int acc) {
+    const int Nc = L1 * L2;
+    const int kq = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kq >= Nc) return;
+    const int l1 = kq % L1, l2 = kq / L1;
+    double re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
+    for (int d = 0; d < Nc; ++d) {
+        const int d1 = d % L1, d2 = d / L1;
+        const double2 w1 = tw1[(l1 * d1) % L1], w2 = tw2[(l2 * d2) % L2];
+        // e^{+i k.d} = conj(w1 w2)
+        const double cr = w1.x * w2.x - w1.y * w2.y;
+        const double ci = -(w1.x * w2.y + w1.y * w2.x);
+        for (int q = 0; q < 4; ++q) {
+            const double v = h[4 * d + q];
+            re[q] = fma(cr, v, re[q]);
+            im[q] = fma(ci, v, im[q]);
+        }
+    }
+    for (int q = 0; q < 4; ++q) {
+        double* o = nk + 2 * (4 * kq + q);
+        if (acc) { o[0] += re[q] / Nc; o[1] += im[q] / Nc; }
+        else     { o[0] = re[q] / Nc; o[1] = im[q] / Nc; }
+    }
+}
+
+// Scalars (one CTA).  out[0..8] = energy, D, ekin, density, m2, S_af, S_af_dk,
+// R_m2, Czz_half; czz_acc (optional) accumulates czz; acc != 0 adds into out;
+// count (optional) is incremented.
+__global__ void k_measure_scalars(const double* __restrict__ g, const double* __restrict__ czz, int L1, int L2,
+                                  double t, double U, const double2* __restrict__ tw1, double* out,
+                                  double* czz_acc, int acc, long long* count, DevStatus* st) {
+    __shared__ double red[33];
+    const int Nc = L1 * L2, N = 2 * Nc;
+    double dsum = 0.0, dens = 0.0, kin = 0.0, s0 = 0.0, sdk = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double gii = g[(size_t)i * N + i];
+        dsum += (1.0 - gii) * gii;
+        dens += (1.0 - gii) + gii;
+    }
+    // bonds A(n1,n2) - B(n1+d1, n2+d2), d in {(0,0), (1,-1), (0,-1)} (Gauge-I, Sec. III.C)
+    for (int I = threadIdx.x; I < Nc; I += blockDim.x) {
+        const int n1 = I % L1, n2 = I / L1;
+        const int dd1[3] = {0, 1, 0}, dd2[3] = {0, -1, -1};
+        for (int e = 0; e < 3; ++e) {
+            const int J = ((n1 + dd1[e] + L1) % L1) + L1 * ((n2 + dd2[e] + L2) % L2);
+            const int i = I, j = Nc + J;
+            kin += 2.0 * t * (g[(size_t)i * N + j] + g[(size_t)j * N + i]);
+        }
+    }
+    for (int d = threadIdx.x; d < Nc; d += blockDim.x) {
+        const double c = czz[d];
+        const double2 w = tw1[d % L1];     // e^{-2 pi i d1 / L1}; S is real so Re e^{+i...} = w.x
+        s0 += c;
+        sdk += c * w.x;
+        if (czz_acc) czz_acc[d] += c;
+    }
+    dsum = block_sum(dsum, red);
+    dens = block_sum(dens, red);
+    kin = block_sum(kin, red);
+    s0 = block_sum(s0, red);
+    sdk = block_sum(sdk, red);
+    if (threadIdx.x == 0) {
+        const double D = dsum / N;
+        double v[OBS_SCALARS];
+        v[0] = (kin + N * U * D) / N;
+        v[1] = D;
+        v[2] = kin / N;
+        v[3] = dens / N;
+        v[4] = s0 / (2.0 * Nc);
+        v[5] = s0;
+        v[6] = sdk;
+        v[7] = 1.0 - sdk / s0;
+        v[8] = czz[(L1 / 2)];
+        bool bad = false;
+        for (int q = 0; q < OBS_SCALARS; ++q) {
+            if (!isfinite(v[q]) && q != 7) bad = true;
+            out[q] = acc ? out[q] + v[q] : v[q];
+        }
+        if (bad) flag_error(st, DERR_NUMERIC, 300);
+        if (count) *count += 1;
+    }
+}
+
+// Weight ratio of flipping site i given G (test hook): out = {R, r}.
+__global__ void k_ratio(const double* __restrict__ G, int N, int i, int s, double dl_p, double dl_m,
+                        double ef_p, double ef_m, double* out) {
+    const double g = G[(size_t)i * N + i];
+    const double dl = s > 0 ? dl_p : dl_m, ef = s > 0 ? ef_p : ef_m;
+    const double r = fma(dl, 1.0 - g, 1.0);
+    out[0] = ef * r * r;
+    out[1] = r;
+}
+
+// Initial field from the counter-based stream: s = +1 iff u(key, 2^62 + l*N + i + 1) < 1/2.
+__global__ void k_init_field(int8_t* s, int M, int N, uint64_t key) {
+    const size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o < (size_t)M * N) s[o] = sm64_uniform(key, (1ull << 62) + o + 1) < 0.5 ? 1 : -1;
+}
+
+}  // namespace afq

@@ -17,6 +17,9 @@ WORKLOADS = {
     "L6_beta6": dict(L=6, beta=6.0, dtau=0.1, U=3.73, n_delay=32, n_stab=10),
     # the headline sweep workload: N = 1152 sites, M = 240 slices
     "L24_beta24": dict(L=24, beta=24.0, dtau=0.1, U=3.73, n_delay=64, n_stab=8),
+    # same N and kernels as the headline workload, 16 slices: small device
+    # footprint for profiler captures
+    "L24_beta1.6": dict(L=24, beta=1.6, dtau=0.1, U=3.73, n_delay=64, n_stab=8),
 }
 
 

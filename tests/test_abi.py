@@ -1,0 +1,56 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every
+entry point include/afqmc.h declares, and rejects bad parameters before any
+device work."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "afqmc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(afqmc_[a-z_A-Z]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    import ctypes
+    from paper_2609_14668_b300 import build
+    build.build()
+    lib = ctypes.CDLL(build.LIB)
+    syms = declared_symbols()
+    assert len(syms) >= 13
+    for s in syms:
+        assert hasattr(lib, s), s
+
+
+def test_binding_names_match_header():
+    import paper_2609_14668_b300 as pkg
+    assert sorted(pkg.EXPORTED) == declared_symbols()
+    for s in declared_symbols():
+        assert callable(getattr(pkg, s))
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("L1", 0, "L1"), ("beta", -1.0, "beta"), ("dtau", 0.0, "dtau"), ("n_stab", 7, "n_stab"),
+    ("n_delay", 0, "n_delay"), ("theta1", 0.25, "twist"), ("hs_channel", 1, "spin channel"),
+    ("precision", 3, "precision"), ("U", -1.0, "U"),
+])
+def test_invalid_parameters_rejected_on_host(field, value, msg):
+    import paper_2609_14668_b300 as pkg
+    p = pkg.make_params(L=3, beta=3.0, dtau=0.1, U=3.73, n_delay=4, n_stab=10)
+    setattr(p, field, value)
+    with pytest.raises(pkg.AfqmcError) as e:
+        pkg.afqmc_create(p)
+    assert e.value.code == 1
+    assert msg.split()[0].lower() in str(e.value).lower()
+
+
+def test_beta_not_multiple_of_dtau():
+    import paper_2609_14668_b300 as pkg
+    p = pkg.make_params(L=3, beta=3.05, dtau=0.1, U=3.73, n_delay=4, n_stab=1)
+    with pytest.raises(pkg.AfqmcError) as e:
+        pkg.afqmc_create(p)
+    assert e.value.code == 1
