@@ -170,11 +170,46 @@ afqmc_status afqmc_set_timing(afqmc_handle* h, int32_t enable);
 /* Totals since afqmc_set_timing (synchronises the stream). */
 afqmc_status afqmc_get_timing(afqmc_handle* h, afqmc_timing* out);
 
+/* Largest sizes accepted by afqmc_update_slice_noalloc. */
+#define AFQMC_NOALLOC_MAX_N 1152
+#define AFQMC_NOALLOC_MAX_NDELAY 64
+
+/* Allocation-free delayed update of one slice, for callers that cannot call
+ * cudaMalloc: code running where the CUDA allocator is off limits (inside a
+ * host allocator or a memory-pool callback, in a process whose device memory
+ * is entirely owned by another framework's caching allocator, or under a
+ * strict no-allocation policy for a real-time loop).  The paper has no
+ * counterpart; it computes exactly what afqmc_update_slice computes.
+ *
+ * The caller passes device pointers on the current device: G_dev (N*N FP64,
+ * row-major, read and overwritten with the updated G) and s_dev (the N int8
+ * field values of slice `slice`, +1/-1, flipped in place where accepted), plus
+ * the sizes and physics parameters (N sites, M slices for the random-number
+ * counter, U, dtau, n_delay) and the random stream (seed, chain, sweep_index,
+ * pass).  All scratch lives in one file-scope __device__ array sized for
+ * N <= AFQMC_NOALLOC_MAX_N and n_delay <= AFQMC_NOALLOC_MAX_NDELAY (about
+ * 1.2 MB, held by every GPU that loads the library until the process exits);
+ * larger sizes return AFQMC_E_INVALID with a message from
+ * afqmc_last_error(NULL).  The call never allocates: no cudaMalloc/cudaFree
+ * and no allocating library routine.
+ *
+ * The first call on a device does a one-time set-up on that device (looks up
+ * the device address of the scratch array and sets the kernel's shared-memory
+ * limit); make that first call before any stream capture.  Every call shares
+ * the one scratch array, so calls that overlap on the GPU (different streams
+ * or threads at the same time) race; serialise them.  The call enqueues on
+ * cuda_stream (NULL = legacy default stream) and synchronises it before
+ * returning; *n_accepted (may be NULL) receives the number of accepted flips. */
+afqmc_status afqmc_update_slice_noalloc(double* G_dev, int8_t* s_dev, int32_t N, int32_t M, int32_t slice,
+                                        int32_t pass, uint64_t sweep_index, double U, double dtau,
+                                        int32_t n_delay, uint64_t seed, int32_t chain, void* cuda_stream,
+                                        int32_t* n_accepted);
+
 /* Sizes of the handle: N, M, Nc. */
 afqmc_status afqmc_dims(const afqmc_handle* h, int32_t* N, int32_t* M, int32_t* Nc);
 
 /* Message of the last failed call on h (never NULL).  With h == NULL: the last
- * afqmc_create failure of this thread. */
+ * failure of afqmc_create or afqmc_update_slice_noalloc on this thread. */
 const char* afqmc_last_error(const afqmc_handle* h);
 
 #ifdef __cplusplus

@@ -72,6 +72,9 @@ _SIGS = {
     "afqmc_det_ratio": ([_H, ctypes.c_int32, ctypes.c_int32, _DP]),
     "afqmc_dims": ([_H, _P(ctypes.c_int32), _P(ctypes.c_int32), _P(ctypes.c_int32)]),
     "afqmc_set_timing": ([_H, ctypes.c_int32]),
+    "afqmc_update_slice_noalloc": ([_DP, _I8P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_uint64, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                    ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p, _P(ctypes.c_int32)]),
     "afqmc_get_timing": ([_H, _P(afqmc_timing)]),
 }
 for _name, _args in _SIGS.items():
@@ -190,6 +193,23 @@ def afqmc_get_timing(h):
     t = afqmc_timing()
     _check(_lib.afqmc_get_timing(h, ctypes.byref(t)), h)
     return {name: (int(t.launches[i]), float(t.ms[i])) for i, name in enumerate(KERNEL_FAMILIES)}
+
+
+NOALLOC_MAX_N = 1152
+NOALLOC_MAX_NDELAY = 64
+
+
+def afqmc_update_slice_noalloc(G_dev_ptr, s_dev_ptr, N, M, slice_, pas, sweep_index, U, dtau, n_delay, seed,
+                               chain=0, stream=None):
+    """Allocation-free slice update on caller-owned device buffers (raw device
+    pointers, e.g. torch tensor .data_ptr()); returns the accepted count."""
+    n = ctypes.c_int32()
+    code = _lib.afqmc_update_slice_noalloc(ctypes.cast(ctypes.c_void_p(G_dev_ptr), _DP),
+                                           ctypes.cast(ctypes.c_void_p(s_dev_ptr), _I8P), N, M, slice_, pas,
+                                           sweep_index, U, dtau, n_delay, seed, chain,
+                                           ctypes.c_void_p(stream or 0), ctypes.byref(n))
+    _check(code, None)
+    return n.value
 
 
 def afqmc_last_error(h=None):

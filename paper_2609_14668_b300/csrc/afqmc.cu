@@ -9,6 +9,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -421,6 +422,57 @@ void green_at(afqmc_handle* h, int l, double* out) {
     form_green(h, cur, a, out);
 }
 
+// ------------------------------------------------------------------ allocation-free slice update
+// One file-scope scratch array for afqmc_update_slice_noalloc (callers that
+// cannot allocate device memory).  Layout, in bytes from the start:
+//   DevStatus | n_acc | ctl[8] | msite[ND] | mcoef[ND] | Gw[W*W] | xw[ND*W] | yw[ND*W] | Xs[ND*N] | Ys[ND*N]
+constexpr size_t NA_ND = AFQMC_NOALLOC_MAX_NDELAY, NA_N = AFQMC_NOALLOC_MAX_N, NA_W = UPD_WMAX;
+constexpr size_t na_align(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t NA_OFF_STATUS = 0;
+constexpr size_t NA_OFF_ACC = na_align(NA_OFF_STATUS + sizeof(DevStatus));
+constexpr size_t NA_OFF_CTL = na_align(NA_OFF_ACC + sizeof(unsigned long long));
+constexpr size_t NA_OFF_SITE = na_align(NA_OFF_CTL + 8 * sizeof(int));
+constexpr size_t NA_OFF_COEF = na_align(NA_OFF_SITE + NA_ND * sizeof(int));
+constexpr size_t NA_OFF_GW = na_align(NA_OFF_COEF + NA_ND * sizeof(double));
+constexpr size_t NA_OFF_XW = na_align(NA_OFF_GW + NA_W * NA_W * sizeof(double));
+constexpr size_t NA_OFF_YW = na_align(NA_OFF_XW + NA_ND * NA_W * sizeof(double));
+constexpr size_t NA_OFF_XS = na_align(NA_OFF_YW + NA_ND * NA_W * sizeof(double));
+constexpr size_t NA_OFF_YS = na_align(NA_OFF_XS + NA_ND * NA_N * sizeof(double));
+constexpr size_t NA_BYTES = na_align(NA_OFF_YS + NA_ND * NA_N * sizeof(double));
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+constexpr int NA_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+unsigned char* g_noalloc_addr[NA_MAX_DEVICES] = {};   // device address of the scratch, per device
+int g_noalloc_sms[NA_MAX_DEVICES] = {};
+
+// One-time set-up on the current device: the device address of the scratch
+// array (the host-side symbol is only a stand-in and must never reach a
+// kernel) and the update kernel's shared-memory limit.
+afqmc_status noalloc_setup(int dev, size_t smem) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (g_noalloc_addr[dev]) return AFQMC_OK;
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) {
+        g_create_error = std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e);
+        return AFQMC_E_CUDA;
+    }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_slice, UPD_THREADS, smem);
+    if (e != cudaSuccess || occ < 1) {
+        g_create_error = std::string("update kernel set-up failed: ") + cudaGetErrorString(e);
+        return AFQMC_E_CUDA;
+    }
+    g_noalloc_sms[dev] = sms;
+    g_noalloc_addr[dev] = static_cast<unsigned char*>(ptr);
+    return AFQMC_OK;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -754,6 +806,75 @@ afqmc_status afqmc_get_timing(afqmc_handle* h, afqmc_timing* out) {
     for (int c = 0; c < AFQMC_K_COUNT; ++c) { out->launches[c] = h->cat_launches[c]; out->ms[c] = h->cat_ms[c]; }
     return check_device(h);
     API_END(h)
+}
+
+afqmc_status afqmc_update_slice_noalloc(double* G_dev, int8_t* s_dev, int32_t N, int32_t M, int32_t slice,
+                                        int32_t pass, uint64_t sweep_index, double U, double dtau,
+                                        int32_t n_delay, uint64_t seed, int32_t chain, void* cuda_stream,
+                                        int32_t* n_accepted) {
+    if (n_accepted) *n_accepted = 0;
+    auto bad = [](const std::string& m) { g_create_error = m; return AFQMC_E_INVALID; };
+    if (!G_dev || !s_dev) return bad("afqmc_update_slice_noalloc: null device pointer");
+    if (N < 2 || N > (int32_t)NA_N)
+        return bad("afqmc_update_slice_noalloc: N = " + std::to_string(N) + " outside [2, " + std::to_string(NA_N) + "]");
+    if (n_delay < 1 || n_delay > (int32_t)NA_ND)
+        return bad("afqmc_update_slice_noalloc: n_delay = " + std::to_string(n_delay) + " outside [1, " +
+                   std::to_string(NA_ND) + "]");
+    if (M < 1 || slice < 1 || slice > M || (pass != 0 && pass != 1) || !(dtau > 0) || !(U >= 0))
+        return bad("afqmc_update_slice_noalloc: bad slice, pass, M, U or dtau");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
+        g_create_error = std::string("afqmc_update_slice_noalloc: cudaGetDevice: ") + cudaGetErrorString(e);
+        return AFQMC_E_CUDA;
+    }
+    const int W = std::min<int>(UPD_WMAX, N);
+    const size_t smem = sizeof(double) * std::max((size_t)W * (W + 1) + 2 * W, (size_t)2 * n_delay * 32);
+    const size_t smem_max = sizeof(double) * std::max((size_t)NA_W * (NA_W + 1) + 2 * NA_W, (size_t)2 * NA_ND * 32);
+    afqmc_status st0 = noalloc_setup(dev, smem_max);
+    if (st0 != AFQMC_OK) return st0;
+    unsigned char* base = g_noalloc_addr[dev];
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    const double gamma = std::acosh(std::exp(dtau * U / 2.0));
+    UpdArgs a{};
+    a.G = G_dev; a.N = N;
+    a.Xs = reinterpret_cast<double*>(base + NA_OFF_XS);
+    a.Ys = reinterpret_cast<double*>(base + NA_OFF_YS);
+    a.msite = reinterpret_cast<int*>(base + NA_OFF_SITE);
+    a.mcoef = reinterpret_cast<double*>(base + NA_OFF_COEF);
+    a.xw = reinterpret_cast<double*>(base + NA_OFF_XW);
+    a.yw = reinterpret_cast<double*>(base + NA_OFF_YW);
+    a.Gw = reinterpret_cast<double*>(base + NA_OFF_GW);
+    a.ctl = reinterpret_cast<int*>(base + NA_OFF_CTL);
+    a.s = s_dev;
+    a.nd = n_delay; a.W = W;
+    a.dl_p = std::exp(-2.0 * gamma) - 1.0; a.dl_m = std::exp(2.0 * gamma) - 1.0;
+    a.ef_p = std::exp(2.0 * gamma);        a.ef_m = std::exp(-2.0 * gamma);
+    a.key = sm64_mix(seed ^ ((uint64_t)(chain + 1) * 0xD1B54A32D192ED03ull));
+    a.ctr0 = ((sweep_index * 2 + (uint64_t)pass) * (uint64_t)M + (uint64_t)(slice - 1)) * (uint64_t)N + 1;
+    a.n_acc = reinterpret_cast<unsigned long long*>(base + NA_OFF_ACC);
+    a.st = reinterpret_cast<DevStatus*>(base + NA_OFF_STATUS);
+    // the scratch keeps the previous call's contents: clear the status, the
+    // grid-barrier counter and the accepted count (everything else is written
+    // before it is read within a call)
+    e = cudaMemsetAsync(base, 0, NA_OFF_CTL, stream);
+    void* args[] = {&a};
+    if (e == cudaSuccess)
+        e = cudaLaunchCooperativeKernel((void*)k_update_slice, g_noalloc_sms[dev], UPD_THREADS, args, smem, stream);
+    DevStatus ds{};
+    unsigned long long acc = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ds, a.st, sizeof(ds), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&acc, a.n_acc, sizeof(acc), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("afqmc_update_slice_noalloc: ") + cudaGetErrorString(e);
+        return AFQMC_E_CUDA;
+    }
+    if (ds.err == DERR_NUMERIC) { g_create_error = "afqmc_update_slice_noalloc: non-finite ratio"; return AFQMC_E_NUMERIC; }
+    if (ds.err == DERR_TIMEOUT) { g_create_error = "afqmc_update_slice_noalloc: device wait timed out"; return AFQMC_E_TIMEOUT; }
+    if (ds.err != 0) { g_create_error = "afqmc_update_slice_noalloc: device error"; return AFQMC_E_CUDA; }
+    if (n_accepted) *n_accepted = (int32_t)acc;
+    return AFQMC_OK;
 }
 
 afqmc_status afqmc_dims(const afqmc_handle* h, int32_t* N, int32_t* M, int32_t* Nc) {
