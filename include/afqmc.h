@@ -31,7 +31,8 @@
  *     and device-side wait timeouts return a status; nothing traps.
  *
  * Scope of this version: periodic boundaries (theta = 0), the spin-channel
- * field (hs_channel = 0), one Markov chain per handle; the real FP64 path.
+ * field (hs_channel = 0), one Markov chain per handle; the real FP64 path,
+ * optionally with a split-TF32 tensor-core flush (precision = 1).
  */
 #ifndef AFQMC_H
 #define AFQMC_H
@@ -65,7 +66,10 @@ typedef struct {
     int32_t hs_channel;    /* 0 = spin channel HS-s^z (Eq. SzHS); only 0 supported */
     int32_t n_delay;       /* delay rank n_d >= 1; 1 is the local Sherman-Morrison update */
     int32_t n_stab;        /* slices between QR recomputations of G; M % n_stab == 0 */
-    int32_t precision;     /* 0 = FP64 everywhere (only 0 supported) */
+    int32_t precision;     /* 0 = FP64 everywhere; 1 = delayed-update flush G -= X Y as three TF32
+                              tensor-core products (hi*hi + hi*lo + lo*hi, FP32 accumulate)
+                              subtracted from the FP64 G; ratios, x/y recursion, wraps,
+                              stabilisation and measurements stay FP64 */
     int32_t measure;       /* 1: accumulate observables at every recomputation of G in a sweep */
     int32_t chain;         /* chain index: selects the random stream */
     int32_t device;        /* CUDA device ordinal */

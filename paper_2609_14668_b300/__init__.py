@@ -217,10 +217,11 @@ def afqmc_last_error(h=None):
     return m.decode() if m else ""
 
 
-def make_params(L, beta, dtau, U, n_delay, n_stab, t=1.0, seed=0, chain=0, measure=0, device=0, L2=None):
+def make_params(L, beta, dtau, U, n_delay, n_stab, t=1.0, seed=0, chain=0, measure=0, device=0, L2=None,
+                precision=0):
     return afqmc_params(L1=L, L2=L if L2 is None else L2, t=t, U=U, beta=beta, dtau=dtau, theta1=0.0, theta2=0.0,
-                        hs_channel=0, n_delay=n_delay, n_stab=n_stab, precision=0, measure=measure, chain=chain,
-                        device=device, seed=seed)
+                        hs_channel=0, n_delay=n_delay, n_stab=n_stab, precision=precision, measure=measure,
+                        chain=chain, device=device, seed=seed)
 
 
 class Chain:

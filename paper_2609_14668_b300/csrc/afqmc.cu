@@ -227,6 +227,14 @@ void qr(afqmc_handle* h, double* At) {
 
 int warp_grid(int ncols) { return (ncols * 32 + 255) / 256; }
 
+// dynamic shared memory of k_update_slice: window block (phase B) or flush tiles (phase F)
+size_t update_smem(int W, int nd, int precision) {
+    size_t b = sizeof(double) * ((size_t)W * (W + 1) + 2 * W);
+    size_t f = sizeof(double) * 2 * (size_t)nd * 32;
+    if (precision == 1) f = std::max(f, sizeof(uint32_t) * 4 * (size_t)((nd + 7) & ~7) * FT);
+    return std::max(b, f);
+}
+
 // out = UDT of (chain of slices lo..hi) applied to `in`:
 //   left  (R chain):  B_hi ... B_lo U D T
 //   !left (L chain):  (B_hi ... B_lo)^T U D T
@@ -317,7 +325,8 @@ void update_slice(afqmc_handle* h, double* G, int l, int pass, uint64_t sweep) {
     a.key = h->key;
     a.ctr0 = ((sweep * 2 + (uint64_t)pass) * (uint64_t)h->M + (uint64_t)(l - 1)) * (uint64_t)h->N + 1;
     a.n_acc = h->n_acc; a.st = h->st;
-    const size_t smem = sizeof(double) * std::max((size_t)h->W * (h->W + 1) + 2 * h->W, (size_t)2 * h->nd * 32);
+    a.precision = h->p.precision;
+    const size_t smem = update_smem(h->W, h->nd, h->p.precision);
     void* args[] = {&a};
     Scope sc(h, AFQMC_K_UPDATE);
     CK(cudaLaunchCooperativeKernel((void*)k_update_slice, h->sms, UPD_THREADS, args, smem, h->stream));
@@ -488,7 +497,7 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
     if (!(P.U >= 0)) return bad("U must be >= 0");
     if (P.theta1 != 0.0 || P.theta2 != 0.0) return bad("twisted boundaries are not supported in this version");
     if (P.hs_channel != 0) return bad("only the spin channel (hs_channel = 0) is supported");
-    if (P.precision != 0) return bad("only precision = 0 (FP64) is supported");
+    if (P.precision != 0 && P.precision != 1) return bad("precision must be 0 (FP64) or 1 (split-TF32 flush)");
     const double Mr = P.beta / P.dtau;
     const int M = (int)std::llround(Mr);
     if (M < 1 || std::fabs(M * P.dtau - P.beta) > 1e-9) return bad("beta must be an integer multiple of dtau");
@@ -538,7 +547,7 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         h->rowop_smem = sizeof(double2) * 2 * (size_t)h->vp * N;
         if (h->rowop_smem > 200 * 1024) throw CudaFail{AFQMC_E_INVALID, "lattice too large for the row kernel"};
         CK(cudaFuncSetAttribute(k_rowop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->rowop_smem));
-        const size_t usmem = sizeof(double) * std::max((size_t)h->W * (h->W + 1) + 2 * h->W, (size_t)2 * h->nd * 32);
+        const size_t usmem = update_smem(h->W, h->nd, P.precision);
         CK(cudaFuncSetAttribute(k_update_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem));
         int occ = 0;
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_slice, UPD_THREADS, usmem));

@@ -43,7 +43,88 @@ struct UpdArgs {
     uint64_t key, ctr0;           // random number of site i is u(key, ctr0 + i)
     unsigned long long* n_acc;
     DevStatus* st;
+    int precision;                // 0: FP64 flush; 1: split-TF32 tensor-core flush, FP32 accumulate
 };
+
+// ---------------------------------------------------------------------------
+// Split-TF32 flush tile (precision 1): G[i0:i0+64, j0:j0+64] -= X Y with
+// X = Xh + Xl, Y = Yh + Yl (each part a TF32 number, from the FP32 rounding of
+// the FP64 value), product Xh Yh + Xh Yl + Xl Yh on the tensor cores with
+// FP32 accumulation (Ootomo & Yokota 2022), subtracted in FP64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t f32_to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_m16n8k8_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+constexpr int FT = 64;   // flush tile edge (precision 1)
+
+// smem: 4 arrays of kp x FT uint32 (kp = k rounded up to 8): Xh, Xl, Yh, Yl.
+__device__ void flush_tile_tf32(const UpdArgs& a, int k, int i0, int j0, uint32_t* sm) {
+    const int N = a.N;
+    const int kp = (k + 7) & ~7;
+    uint32_t* xh = sm;
+    uint32_t* xl = xh + kp * FT;
+    uint32_t* yh = xl + kp * FT;
+    uint32_t* yl = yh + kp * FT;
+    __syncthreads();
+    for (int o = threadIdx.x; o < kp * FT; o += blockDim.x) {
+        const int m = o / FT, q = o - m * FT;
+        double xv = 0.0, yv = 0.0;
+        if (m < k) {
+            if (i0 + q < N) xv = __ldcg(a.Xs + (size_t)m * N + i0 + q);
+            if (j0 + q < N) yv = __ldcg(a.Ys + (size_t)m * N + j0 + q);
+        }
+        const float xf = (float)xv, yf = (float)yv;
+        const uint32_t xhi = f32_to_tf32(xf), yhi = f32_to_tf32(yf);
+        xh[o] = xhi; xl[o] = f32_to_tf32(xf - __uint_as_float(xhi));
+        yh[o] = yhi; yl[o] = f32_to_tf32(yf - __uint_as_float(yhi));
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int r0 = 16 * (warp >> 1);          // 4 row blocks of 16
+    const int c0 = 32 * (warp & 1);           // 2 column blocks of 32 (4 n8 tiles)
+    float acc[4][4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[n][q] = 0.f;
+    for (int k0 = 0; k0 < kp; k0 += 8) {
+        const int ka = (k0 + t) * FT, kb = (k0 + t + 4) * FT;
+        const uint32_t ah[4] = {xh[ka + r0 + g], xh[ka + r0 + g + 8], xh[kb + r0 + g], xh[kb + r0 + g + 8]};
+        const uint32_t al[4] = {xl[ka + r0 + g], xl[ka + r0 + g + 8], xl[kb + r0 + g], xl[kb + r0 + g + 8]};
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            const int cc = c0 + 8 * n + g;
+            const uint32_t bh0 = yh[ka + cc], bh1 = yh[kb + cc];
+            const uint32_t bl0 = yl[ka + cc], bl1 = yl[kb + cc];
+            mma_m16n8k8_tf32(acc[n], al, bh0, bh1);
+            mma_m16n8k8_tf32(acc[n], ah, bl0, bl1);
+            mma_m16n8k8_tf32(acc[n], ah, bh0, bh1);
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        const int col = j0 + c0 + 8 * n + 2 * t;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int row = i0 + r0 + g + 8 * h;
+            if (row >= N) continue;
+            double* gp = a.G + (size_t)row * N + col;
+            if (col < N) gp[0] = __ldcg(gp) - (double)acc[n][2 * h];
+            if (col + 1 < N) gp[1] = __ldcg(gp + 1) - (double)acc[n][2 * h + 1];
+        }
+    }
+}
 
 __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
     extern __shared__ double upd_smem[];
@@ -174,30 +255,36 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
         const bool done = (c1 >= N);
         // ------------------------------------------------------------ phase F
         if (k > 0 && (k == nd || done)) {
-            double* xs = upd_smem;               // k x 32
-            double* ys = upd_smem + nd * 32;     // k x 32
-            const int nt = (N + 31) / 32;
-            for (int tile = blockIdx.x; tile < nt * nt; tile += gridDim.x) {
-                const int i0 = (tile / nt) * 32, j0 = (tile % nt) * 32;
-                __syncthreads();
-                for (int o = threadIdx.x; o < k * 32; o += blockDim.x) {
-                    const int m = o / 32, q = o % 32;
-                    xs[o] = (i0 + q < N) ? __ldcg(a.Xs + (size_t)m * N + i0 + q) : 0.0;
-                    ys[o] = (j0 + q < N) ? __ldcg(a.Ys + (size_t)m * N + j0 + q) : 0.0;
-                }
-                __syncthreads();
-                for (int o = threadIdx.x; o < 32 * 32; o += blockDim.x) {
-                    const int ii = o / 32, jj = o % 32;
-                    if (i0 + ii >= N || j0 + jj >= N) continue;
-                    double acc0 = 0.0, acc1 = 0.0;
-                    int m = 0;
-                    for (; m + 1 < k; m += 2) {
-                        acc0 = fma(xs[m * 32 + ii], ys[m * 32 + jj], acc0);
-                        acc1 = fma(xs[(m + 1) * 32 + ii], ys[(m + 1) * 32 + jj], acc1);
+            if (a.precision == 1) {
+                const int nt = (N + FT - 1) / FT;
+                for (int tile = blockIdx.x; tile < nt * nt; tile += gridDim.x)
+                    flush_tile_tf32(a, k, (tile / nt) * FT, (tile % nt) * FT, reinterpret_cast<uint32_t*>(upd_smem));
+            } else {
+                double* xs = upd_smem;               // k x 32
+                double* ys = upd_smem + nd * 32;     // k x 32
+                const int nt = (N + 31) / 32;
+                for (int tile = blockIdx.x; tile < nt * nt; tile += gridDim.x) {
+                    const int i0 = (tile / nt) * 32, j0 = (tile % nt) * 32;
+                    __syncthreads();
+                    for (int o = threadIdx.x; o < k * 32; o += blockDim.x) {
+                        const int m = o / 32, q = o % 32;
+                        xs[o] = (i0 + q < N) ? __ldcg(a.Xs + (size_t)m * N + i0 + q) : 0.0;
+                        ys[o] = (j0 + q < N) ? __ldcg(a.Ys + (size_t)m * N + j0 + q) : 0.0;
                     }
-                    if (m < k) acc0 = fma(xs[m * 32 + ii], ys[m * 32 + jj], acc0);
-                    double* gp = a.G + (size_t)(i0 + ii) * N + j0 + jj;
-                    *gp = __ldcg(gp) - (acc0 + acc1);
+                    __syncthreads();
+                    for (int o = threadIdx.x; o < 32 * 32; o += blockDim.x) {
+                        const int ii = o / 32, jj = o % 32;
+                        if (i0 + ii >= N || j0 + jj >= N) continue;
+                        double acc0 = 0.0, acc1 = 0.0;
+                        int m = 0;
+                        for (; m + 1 < k; m += 2) {
+                            acc0 = fma(xs[m * 32 + ii], ys[m * 32 + jj], acc0);
+                            acc1 = fma(xs[(m + 1) * 32 + ii], ys[(m + 1) * 32 + jj], acc1);
+                        }
+                        if (m < k) acc0 = fma(xs[m * 32 + ii], ys[m * 32 + jj], acc0);
+                        double* gp = a.G + (size_t)(i0 + ii) * N + j0 + jj;
+                        *gp = __ldcg(gp) - (acc0 + acc1);
+                    }
                 }
             }
             k = 0;

@@ -1,0 +1,69 @@
+"""The split-TF32 flush (precision = 1): G -= X Y as Xh Yh + Xh Yl + Xl Yh on the
+tensor cores with FP32 accumulation, subtracted from the FP64 G.
+
+Tolerance (derived from the arithmetic): X and Y are first rounded to FP32
+(relative 2^-24); the three TF32 products drop only the lo*lo term (2^-22);
+FP32 accumulation over n_delay <= 64 terms adds at most 64 * 2^-24.  One flush
+therefore perturbs G by <~ 1e-6 * max|X| max|Y| * n_delay; a slice holds up to
+N / n_delay flushes and G is recomputed in FP64 every n_stab slices.  The
+tests hold G after one slice to 2e-6 relative of the oracle, decisions
+(fields) to exact agreement, and observables of a multi-sweep chain to 1e-5
+relative of the FP64 chain with the same random numbers."""
+import numpy as np
+import pytest
+
+from synth import random_field, WORKLOADS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2609_14668_b300 as p
+    return p
+
+
+def rel_err(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("key,n_delay", [("L6_beta6", 32), ("L6_beta6", 8), ("L24_beta1.6", 64)])
+def test_tf32_slice_update_vs_oracle(pkg, key, n_delay):
+    from oracle.dqmc import Model, Chain
+    w = WORKLOADS[key]
+    beta = min(w["beta"], 1.6)
+    m = Model(w["L"], U=w["U"], beta=beta, dtau=w["dtau"])
+    f = random_field(m.M, m.N, 71)
+    ch = pkg.Chain(pkg.make_params(L=w["L"], beta=beta, dtau=w["dtau"], U=w["U"], n_delay=n_delay, n_stab=8,
+                                   seed=13, precision=1))
+    ch.set_field(f)
+    G1 = m.wrap(m.green_stable(f, 0, 8), f[0])
+    oc = Chain(m, n_delay=n_delay, n_stab=8, seed=13, field=f)
+    oc.G = G1.copy()
+    oc.update_slice(1, 0)
+    Gg, nacc = pkg.afqmc_update_slice(ch.h, 1, 0, 0, G1)
+    assert nacc == oc.accepted > 0
+    assert np.array_equal(ch.field()[0], oc.field[0])
+    err = rel_err(Gg, oc.G)
+    assert err < 2e-6, err
+    ch.close()
+
+
+def test_tf32_chain_vs_fp64_chain(pkg):
+    w = WORKLOADS["L6_beta6"]
+    chains = [pkg.Chain(pkg.make_params(L=w["L"], beta=w["beta"], dtau=w["dtau"], U=w["U"], n_delay=w["n_delay"],
+                                        n_stab=w["n_stab"], seed=2025, measure=1, precision=p)) for p in (0, 1)]
+    obs = []
+    for ch in chains:
+        ch.sweep(3)
+        obs.append(ch.observables())
+    assert np.array_equal(chains[0].field(), chains[1].field())
+    for k in ("energy", "double_occ", "S_af", "m2"):
+        assert abs(obs[1][k] - obs[0][k]) <= 1e-5 * abs(obs[0][k]), (k, obs[0][k], obs[1][k])
+    G0, G1 = chains[0].green(0), chains[1].green(0)
+    assert rel_err(G1, G0) < 1e-10      # same field: the recomputed G is FP64 in both modes
+    for ch in chains:
+        ch.close()
