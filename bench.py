@@ -4,6 +4,9 @@
 One step = one full sweep (forward + backward pass over all M slices: wraps,
 delayed updates, QR recomputations of G, measurements) of one Markov chain.
 The metric is proposed single-site HS-field flips per second: 2 N M per sweep.
+The headline value is the L = 24 precision workload (delayed-update flush as
+split-TF32 tensor-core products, everything else FP64); the plain FP64 sweep
+on the same seed is timed after it and reported under "fp64".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -32,6 +35,17 @@ WORKLOAD_KEY = "L24_beta24"
 FP64_PEAK_TFLOPS = 1.25      # nominal B300 FP64 rate (SIMT and tensor); DFMA microbenchmark on this pool: 1.13
 
 
+def _tf32_peak():
+    # measured BF16 dense burst (MEASURED_PEAKS.json) x nominal TF32/BF16 ratio 1.1/2.25
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] * 1.1 / 2.25
+    except Exception:
+        return 1800.0 * 1.1 / 2.25
+
+
+TF32_PEAK_TFLOPS = _tf32_peak()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -41,6 +55,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD_KEY, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],
+                    help="1: split-TF32 tensor-core flush (the L=24 precision workload); 0: plain FP64")
+    ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 sweep")
     return ap.parse_args()
 
 
@@ -214,23 +231,13 @@ def algorithmic_flops(family, N, Nc, accepted_per_update):
     return None
 
 
-def run_ours(args):
-    import torch
-    import paper_2609_14668_b300 as pkg
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group(backend="nccl")
-    dev = local if world > 1 else 0
-    key = args.workload
+def time_chain(pkg, torch, args, key, precision, rank, world, dev, dist, stream):
+    """Create one chain, run W warm-up sweeps, time K sweeps with CUDA events on
+    the library's stream (per-launch timing enabled).  Returns a result dict."""
     w, N, M = workload_config(key)
-    stream = torch.cuda.Stream(device=dev)
     params = pkg.make_params(L=w["L"], beta=w["beta"], dtau=w["dtau"], U=w["U"], n_delay=w["n_delay"],
-                             n_stab=w["n_stab"], seed=1000 + rank, chain=rank, measure=1, device=dev)
+                             n_stab=w["n_stab"], seed=1000 + rank, chain=rank, measure=1, device=dev,
+                             precision=precision)
     ch = pkg.Chain(params, stream=stream.cuda_stream)
     for _ in range(args.warmup):
         ch.sweep(1)
@@ -263,8 +270,7 @@ def run_ours(args):
     timing = pkg.afqmc_get_timing(ch.h)
     pkg.afqmc_set_timing(ch.h, 0)
     obs = ch.observables()
-    ms_max = ms
-    total_proposed = proposed
+    ms_max, total_proposed = ms, proposed
     if dist is not None:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -272,7 +278,58 @@ def run_ours(args):
         p = torch.tensor([float(proposed)], dtype=torch.float64, device=dev)
         dist.all_reduce(p, op=dist.ReduceOp.SUM)
         total_proposed = float(p.item())
-    value = total_proposed / (ms_max / 1e3)
+    return dict(chain=ch, ms=ms_max, value=total_proposed / (ms_max / 1e3), proposed=proposed,
+                total_proposed=total_proposed, accepted=accepted, launches=launches, drift=drift,
+                timing=timing, obs=obs, clocks=ck, barrier=barrier)
+
+
+def roofline_of(timing, N, accepted, precision):
+    """Roofline of the kernel family with the most device time."""
+    import math
+    Nc = N // 2
+    fam = max((k for k in timing if timing[k][0] > 0), key=lambda k: timing[k][1])
+    nl, tms = timing[fam]
+    acc_per_update = accepted / max(timing["update"][0], 1)
+    if fam == "update" and precision == 1:
+        # flush on the tensor cores: 3 TF32 products of 2 N^2 flops per accepted flip
+        fl = 3 * 2.0 * N * N * acc_per_update
+        peak, bound, unit = TF32_PEAK_TFLOPS, "tensor", "TFLOP/s"
+        note = "TF32 dense = measured BF16 burst x nominal TF32/BF16 ratio (1.1/2.25)"
+    else:
+        fl = algorithmic_flops(fam, N, Nc, acc_per_update)
+        peak, bound, unit = FP64_PEAK_TFLOPS, "alu", "TFLOP/s"
+        note = "nominal B300 FP64 (DFMA microbenchmark on this pool: 1.13 TFLOP/s)"
+    if fl is None:
+        return None
+    ach = fl / (tms / nl / 1e3) / 1e12
+    return {"bound": bound, "kernel": fam, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+            "traffic": None, "peak_note": note, "flops_per_launch": fl, "avg_launch_ms": tms / nl,
+            "share_of_step": tms / sum(v[1] for v in timing.values())}
+
+
+def run_ours(args):
+    import torch
+    import paper_2609_14668_b300 as pkg
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group(backend="nccl")
+    dev = local if world > 1 else 0
+    key = args.workload
+    w, N, M = workload_config(key)
+    stream = torch.cuda.Stream(device=dev)
+    # headline: the reduced-precision workload (split-TF32 flush); then the plain FP64 sweep
+    head = time_chain(pkg, torch, args, key, args.precision, rank, world, dev, dist, stream)
+    ref64 = None
+    if args.precision != 0 and not args.no_fp64:
+        ref64 = time_chain(pkg, torch, args, key, 0, rank, world, dev, dist, stream)
+        ref64["chain"].close()
+    ch = head["chain"]
+    barrier = head["barrier"]
 
     # e2e: the public call a user makes per step (one sweep) plus reading the step's
     # results back to host memory (observable averages and the field); state stays resident.
@@ -288,44 +345,39 @@ def run_ours(args):
             nbytes = 10 * 8 + o["Czz"].nbytes + o["nk"].nbytes + f.nbytes
         barrier()
         wall = time.perf_counter() - t0
-        e2e_val = proposed / wall
+        e2e_val = head["proposed"] / wall
         if dist is not None:
             t = torch.tensor([wall], dtype=torch.float64, device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_val = total_proposed / float(t.item())
+            e2e_val = head["total_proposed"] / float(t.item())
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": nbytes}
 
-    # roofline of the dominant kernel family (most device time in the timed region)
-    Nc = N // 2
-    n_update = timing["update"][0]
-    acc_per_update = accepted / max(n_update, 1)
-    fam = max((k for k in timing if timing[k][0] > 0), key=lambda k: timing[k][1])
-    nl, tms = timing[fam]
-    fl = algorithmic_flops(fam, N, Nc, acc_per_update)
-    roof = None
-    if fl is not None:
-        ach = fl / (tms / nl / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": fam, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_note": "nominal B300 FP64 (DFMA microbenchmark on this pool: 1.13 TFLOP/s)",
-                "flops_per_launch": fl, "avg_launch_ms": tms / nl}
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+    out = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.precision == 0 else "f64 (flush: tf32x3, f32 accumulate)",
            "data": "synthetic (random initial Ising field from the seed; no dataset)",
            "config": {"workload": key, "L": w["L"], "N_sites": N, "beta": w["beta"], "dtau": w["dtau"], "M": M,
-                      "U": w["U"], "n_delay": w["n_delay"], "n_stab": w["n_stab"], "chains_per_gpu": 1,
-                      "parallelism": f"replicas{world}",
+                      "U": w["U"], "n_delay": w["n_delay"], "n_stab": w["n_stab"], "precision": args.precision,
+                      "chains_per_gpu": 1, "parallelism": f"replicas{world}",
                       "l2": "no flush: a sweep streams the UDT stacks (1.3 GB) through the 126 MB L2"},
-           "roofline": roof,
-           "gpu_launches": int(launches),
-           "acceptance": accepted / max(proposed, 1), "max_stab_drift": drift,
-           "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in timing.items()},
-           "observables": {k: obs[k] for k in ("energy", "double_occ", "m2", "n_samples")}}
+           "roofline": roofline_of(head["timing"], N, head["accepted"], args.precision),
+           "gpu_launches": int(head["launches"]),
+           "acceptance": head["accepted"] / max(head["proposed"], 1), "max_stab_drift": head["drift"],
+           "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in head["timing"].items()},
+           "observables": {k: head["obs"][k] for k in ("energy", "double_occ", "S_af", "m2", "n_samples")}}
+    if ref64 is not None:
+        rel = {k: abs(head["obs"][k] - ref64["obs"][k]) / max(abs(ref64["obs"][k]), 1e-300)
+               for k in ("energy", "double_occ", "S_af")}
+        out["fp64"] = {"value": ref64["value"], "ms_per_step": ref64["ms"] / args.steps,
+                       "speedup": head["value"] / ref64["value"],
+                       "obs_rel_diff_vs_fp64": rel,
+                       "kernel_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in ref64["timing"].items()},
+                       "roofline": roofline_of(ref64["timing"], N, ref64["accepted"], 0)}
     if e2e:
         out["e2e"] = e2e
-    if ck:
-        out["clocks"] = ck
+    if head["clocks"]:
+        out["clocks"] = head["clocks"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(key)
     ch.close()

@@ -34,5 +34,20 @@ def build(force=False, verbose=False):
     return LIB
 
 
+def build_peak(verbose=False):
+    """Standalone FP64/FP32/barrier microbenchmark (fp64_peak)."""
+    out = os.path.join(HERE, "fp64_peak")
+    nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+    cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", out, os.path.join(HERE, "csrc", "fp64_peak.cu")]
+    if verbose:
+        print(" ".join(cmd))
+    subprocess.run(cmd, check=True)
+    return out
+
+
 if __name__ == "__main__":
-    build(force=True, verbose=True)
+    import sys
+    if "--peak" in sys.argv:
+        build_peak(verbose=True)
+    else:
+        build(force=True, verbose=True)

@@ -9,6 +9,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -107,11 +108,13 @@ struct afqmc_handle {
 namespace {
 
 // ------------------------------------------------------------------ set-up
-void factor_pair(int n, int& a, int& b) {
-    a = 1;
-    for (int d = 2; d * d <= n; ++d)
-        if (n % d == 0) a = d;
-    b = n / a;
+// radices of an L-point FFT: 4s first, then 2, 3, then the remaining primes
+int radices(int n, int* r) {
+    int k = 0;
+    while (n % 4 == 0 && k < FFT_MAX_STAGES) { r[k++] = 4; n /= 4; }
+    for (int p = 2; n > 1 && k < FFT_MAX_STAGES; ++p)
+        while (n % p == 0 && k < FFT_MAX_STAGES) { r[k++] = p; n /= p; }
+    return n == 1 ? k : -1;
 }
 
 // f(k) = -t [1 + e^{i k.(a1-a2)} + e^{-i k.a2}] (below Eq. h0kMat),
@@ -131,6 +134,23 @@ void block_exp(std::complex<double> f, double c, double2 out[4]) {
     out[1] = make_double2(sf.real(), sf.imag());
     out[2] = make_double2(sf.real(), -sf.imag());
     out[3] = make_double2(ch, 0.0);
+}
+
+// The dynamic shared-memory limit of a kernel is process-wide state of the
+// device: only ever raise it, so handles of different sizes can coexist.
+std::mutex g_attr_mutex;
+std::map<std::pair<int, const void*>, size_t> g_attr_max;
+
+cudaError_t raise_smem_limit(const void* func, size_t bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    size_t& cur = g_attr_max[{dev, func}];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
 }
 
 void set_error(afqmc_handle* h, afqmc_status code, const std::string& msg) {
@@ -200,9 +220,9 @@ DiagScale vscale(afqmc_handle* h, int l, int sign) {   // e^{sign gamma s_l}
 }
 
 void gemm(afqmc_handle* h, const double* A, int transA, const double* B, int transB, double* C, double alpha,
-          double beta, const double* rs, int rs_inv, const double* cs, int cs_inv) {
+          double beta, const double* rs, int rs_inv, const double* cs, int cs_inv, int a_upper = 0) {
     const int n = h->N;
-    GemmArgs g{A, B, C, n, n, n, n, n, n, transA, transB, alpha, beta, rs, cs, rs_inv, cs_inv};
+    GemmArgs g{A, B, C, n, n, n, n, n, n, transA, transB, alpha, beta, rs, cs, rs_inv, cs_inv, a_upper};
     dim3 grid((n + GT - 1) / GT, (n + GT - 1) / GT);
     Scope sc(h, AFQMC_K_GEMM);
     k_dgemm<<<grid, 256, 0, h->stream>>>(g);
@@ -226,12 +246,17 @@ void qr(afqmc_handle* h, double* At) {
 }
 
 int warp_grid(int ncols) { return (ncols * 32 + 255) / 256; }
+int cpb_grid(int ncols) { return (ncols + CPB - 1) / CPB; }
+size_t cpb_smem(int n) { return sizeof(double) * (size_t)(CPB + 2) * n; }
 
 // dynamic shared memory of k_update_slice: window block (phase B) or flush tiles (phase F)
-size_t update_smem(int W, int nd, int precision) {
-    size_t b = sizeof(double) * ((size_t)W * (W + 1) + 2 * W);
+size_t update_smem(int W, int nd, int precision, int N = AFQMC_NOALLOC_MAX_N, int grid = 148) {
+    size_t b = sizeof(double) * ((size_t)W * (W + 1) + 3 * W);
+    const size_t jpb = (size_t)((N + grid - 1) / grid);
+    b = std::max(b, sizeof(double) * (2 * (size_t)nd * jpb + 2 * (size_t)nd * W + 2 * (size_t)W * W));   // phase C staging
     size_t f = sizeof(double) * 2 * (size_t)nd * 32;
     if (precision == 1) f = std::max(f, sizeof(uint32_t) * 4 * (size_t)((nd + 7) & ~7) * FT);
+    if (precision == 2) f = std::max(f, sizeof(uint32_t) * 4 * (size_t)((nd + 7) & ~7) * TCT);
     return std::max(b, f);
 }
 
@@ -256,11 +281,11 @@ void udt_extend(afqmc_handle* h, const UDTe& in, const UDTe& out, int lo, int hi
     qr(h, AP);
     double* F = h->Wk[2];
     { Scope sc(h, AFQMC_K_QRAUX); k_make_F<<<n, 256, 0, h->stream>>>(AP, h->Dp, F, out.D, h->sgn, n, h->st); }
-    { Scope sc(h, AFQMC_K_QRAUX); k_form_q<<<warp_grid(n), 256, 0, h->stream>>>(AP, h->tau, h->sgn, out.Ut, n); }
+    { Scope sc(h, AFQMC_K_QRAUX); k_form_q<<<cpb_grid(n), 256, cpb_smem(n), h->stream>>>(AP, h->tau, h->sgn, out.Ut, n); }
     double* Tp = h->Wk[3];
     { Scope sc(h, AFQMC_K_QRAUX); k_gather_rows<<<n, 256, 0, h->stream>>>(in.T, Tp, h->perm, nullptr, nullptr, n); }
     CK(cudaGetLastError());
-    gemm(h, F, 0, Tp, 0, out.T, 1.0, 0.0, nullptr, 0, nullptr, 0);
+    gemm(h, F, 0, Tp, 0, out.T, 1.0, 0.0, nullptr, 0, nullptr, 0, /*a_upper=*/1);
 }
 
 // G = (1 + R L)^-1 with R = U_R D_R T_R, L^T = U_L D_L T_L (Loh-Gubernatis split).
@@ -279,9 +304,9 @@ void form_green(afqmc_handle* h, const UDTe& R, const UDTe& Lt, double* Gout) {
         Scope sc(h, AFQMC_K_QRAUX);
         k_transpose_scale<<<g, b, 0, h->stream>>>(R.Ut, Yt, n, n, h->DbR, 1, nullptr, 0);
     }
-    { Scope sc(h, AFQMC_K_QRAUX); k_apply_qt<<<warp_grid(n), 256, 0, h->stream>>>(Mt, h->tau, Yt, n, n); }
+    { Scope sc(h, AFQMC_K_QRAUX); k_apply_qt<<<cpb_grid(n), 256, cpb_smem(n), h->stream>>>(Mt, h->tau, Yt, n, n); }
     double* Wt = h->Wk[2];
-    { Scope sc(h, AFQMC_K_QRAUX); k_backsolve<<<warp_grid(n), 256, 0, h->stream>>>(Mt, Yt, Wt, n, n, h->DbL, h->st); }
+    { Scope sc(h, AFQMC_K_QRAUX); k_backsolve<<<cpb_grid(n), 256, cpb_smem(n), h->stream>>>(Mt, Yt, Wt, n, n, h->DbL, h->st); }
     CK(cudaGetLastError());
     gemm(h, Lt.Ut, 1, Wt, 1, Gout, 1.0, 0.0, nullptr, 0, nullptr, 0);
 }
@@ -326,7 +351,7 @@ void update_slice(afqmc_handle* h, double* G, int l, int pass, uint64_t sweep) {
     a.ctr0 = ((sweep * 2 + (uint64_t)pass) * (uint64_t)h->M + (uint64_t)(l - 1)) * (uint64_t)h->N + 1;
     a.n_acc = h->n_acc; a.st = h->st;
     a.precision = h->p.precision;
-    const size_t smem = update_smem(h->W, h->nd, h->p.precision);
+    const size_t smem = update_smem(h->W, h->nd, h->p.precision, h->N, h->sms);
     void* args[] = {&a};
     Scope sc(h, AFQMC_K_UPDATE);
     CK(cudaLaunchCooperativeKernel((void*)k_update_slice, h->sms, UPD_THREADS, args, smem, h->stream));
@@ -470,7 +495,7 @@ afqmc_status noalloc_setup(int dev, size_t smem) {
     }
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_update_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = raise_smem_limit((const void*)k_update_slice, smem);
     int occ = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_slice, UPD_THREADS, smem);
     if (e != cudaSuccess || occ < 1) {
@@ -497,7 +522,8 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
     if (!(P.U >= 0)) return bad("U must be >= 0");
     if (P.theta1 != 0.0 || P.theta2 != 0.0) return bad("twisted boundaries are not supported in this version");
     if (P.hs_channel != 0) return bad("only the spin channel (hs_channel = 0) is supported");
-    if (P.precision != 0 && P.precision != 1) return bad("precision must be 0 (FP64) or 1 (split-TF32 flush)");
+    if (P.precision < 0 || P.precision > 2) return bad("precision must be 0 (FP64) or 1 (split-TF32 flush)");
+    if (P.precision == 2 && P.n_delay > 64) return bad("the tcgen05 flush supports n_delay <= 64");
     const double Mr = P.beta / P.dtau;
     const int M = (int)std::llround(Mr);
     if (M < 1 || std::fabs(M * P.dtau - P.beta) > 1e-9) return bad("beta must be an integer multiple of dtau");
@@ -523,8 +549,11 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         // FFT plan, twiddles, propagator blocks
         FFTPlan& pl = h->plan;
         pl.N = N; pl.Nc = Nc; pl.L1 = h->L1; pl.L2 = h->L2;
-        factor_pair(h->L1, pl.a1, pl.b1);
-        factor_pair(h->L2, pl.a2, pl.b2);
+        pl.nr1 = radices(h->L1, pl.r1);
+        pl.nr2 = radices(h->L2, pl.r2);
+        for (int q = 0; q < pl.nr1; ++q) if (pl.r1[q] > 8) pl.nr1 = -1;
+        for (int q = 0; q < pl.nr2; ++q) if (pl.r2[q] > 8) pl.nr2 = -1;
+        if (pl.nr1 < 0 || pl.nr2 < 0) throw CudaFail{AFQMC_E_INVALID, "L1 and L2 must factor into primes <= 7"};
         std::vector<double2> t1(h->L1), t2(h->L2);
         for (int m = 0; m < h->L1; ++m) t1[m] = make_double2(std::cos(2 * M_PI * m / h->L1), -std::sin(2 * M_PI * m / h->L1));
         for (int m = 0; m < h->L2; ++m) t2[m] = make_double2(std::cos(2 * M_PI * m / h->L2), -std::sin(2 * M_PI * m / h->L2));
@@ -546,9 +575,12 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         h->vp = std::max(1, std::min(4, (int)(48000 / (sizeof(double2) * 2 * (size_t)N))));
         h->rowop_smem = sizeof(double2) * 2 * (size_t)h->vp * N;
         if (h->rowop_smem > 200 * 1024) throw CudaFail{AFQMC_E_INVALID, "lattice too large for the row kernel"};
-        CK(cudaFuncSetAttribute(k_rowop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->rowop_smem));
-        const size_t usmem = update_smem(h->W, h->nd, P.precision);
-        CK(cudaFuncSetAttribute(k_update_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usmem));
+        CK(raise_smem_limit((const void*)k_rowop, h->rowop_smem));
+        if (N > PRE * 256) throw CudaFail{AFQMC_E_INVALID, "lattice too large for the column kernels"};
+        for (const void* f : {(const void*)k_apply_qt, (const void*)k_form_q, (const void*)k_backsolve})
+            CK(raise_smem_limit(f, cpb_smem(N)));
+        const size_t usmem = update_smem(h->W, h->nd, P.precision, N, h->sms);
+        CK(raise_smem_limit((const void*)k_update_slice, usmem));
         int occ = 0;
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_slice, UPD_THREADS, usmem));
         if (occ < 1) throw CudaFail{AFQMC_E_INVALID, "update kernel does not fit on an SM"};
@@ -557,7 +589,7 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
             const size_t qs = sizeof(double) * (size_t)N * (1 + (N + qg - 1) / qg);
             h->qr_smem_cols = qs <= 200 * 1024;
             const size_t qsm = h->qr_smem_cols ? qs : sizeof(double) * N;
-            CK(cudaFuncSetAttribute(k_qr_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));
+            CK(raise_smem_limit((const void*)k_qr_cols, qsm));
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_qr_cols, 256, qsm));
             if (occ < 1) throw CudaFail{AFQMC_E_INVALID, "QR kernel does not fit on an SM"};
         }
@@ -838,8 +870,14 @@ afqmc_status afqmc_update_slice_noalloc(double* G_dev, int8_t* s_dev, int32_t N,
         return AFQMC_E_CUDA;
     }
     const int W = std::min<int>(UPD_WMAX, N);
-    const size_t smem = sizeof(double) * std::max((size_t)W * (W + 1) + 2 * W, (size_t)2 * n_delay * 32);
-    const size_t smem_max = sizeof(double) * std::max((size_t)NA_W * (NA_W + 1) + 2 * NA_W, (size_t)2 * NA_ND * 32);
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || sms < 1) {
+        g_create_error = std::string("afqmc_update_slice_noalloc: SM count: ") + cudaGetErrorString(e);
+        return AFQMC_E_CUDA;
+    }
+    const size_t smem = update_smem(W, n_delay, 0, N, sms);
+    const size_t smem_max = update_smem((int)NA_W, (int)NA_ND, 0, (int)NA_N, sms);
     afqmc_status st0 = noalloc_setup(dev, smem_max);
     if (st0 != AFQMC_OK) return st0;
     unsigned char* base = g_noalloc_addr[dev];

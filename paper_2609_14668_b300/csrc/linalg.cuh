@@ -28,6 +28,7 @@ struct GemmArgs {
     double alpha, beta;
     const double* rs; const double* cs;   // optional (nullptr = 1)
     int rs_inv, cs_inv;                   // 1: scale by the reciprocal
+    int a_upper;                          // 1: op(A) is upper triangular, skip the zero blocks p < i
 };
 
 // 32 x 32 output tiles (1296 CTAs at N = 1152: 8.8 per SM, so the last wave is
@@ -41,7 +42,8 @@ __global__ void __launch_bounds__(256) k_dgemm(GemmArgs g) {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
     double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
-    for (int p0 = 0; p0 < g.k; p0 += GK) {
+    const int pstart = g.a_upper ? (i0 / GK) * GK : 0;
+    for (int p0 = pstart; p0 < g.k; p0 += GK) {
         for (int o = threadIdx.x; o < GK * GT; o += 256) {
             int pp, ii;
             if (g.transA) { pp = o / GT; ii = o % GT; } else { ii = o / GK; pp = o % GK; }
@@ -232,80 +234,156 @@ __global__ void __launch_bounds__(256) k_qr_cols(QRArgs q, int cols_in_smem) {
     }
 }
 
-// Apply Q^T = H_{n-2} ... H_0 to every column of Y (Yt row-major, ncols columns
-// of length n), i.e. H_0 first.  One warp per column.
-__global__ void __launch_bounds__(256) k_apply_qt(const double* __restrict__ Vt, const double* __restrict__ tau,
-                                                  double* Yt, int n, int ncols) {
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// ---------------------------------------------------------------------------
+// Column-parallel kernels on 8 columns per CTA (one warp each).  The 8 columns
+// stay in shared memory; the vector every column needs at step j (reflector
+// v_j, or column i of R) is staged once per step in shared memory for all 8
+// warps, with the next step's vector prefetched into registers while the
+// current step computes.  Dynamic shared memory: (CPB + 2) * n doubles.
+// ---------------------------------------------------------------------------
+constexpr int CPB = 8;    // columns per CTA
+
+__device__ __forceinline__ double dot4(const double* __restrict__ a, const double* __restrict__ b, int lo, int hi) {
     const int lane = threadIdx.x & 31;
-    if (gw >= ncols) return;
-    double* y = Yt + (size_t)gw * n;
-    for (int j = 0; j < n - 1; ++j) {
-        const double tj = __ldg(tau + j);
-        if (tj == 0.0) continue;
-        const double* vj = Vt + (size_t)j * n;
-        double w = lane == 0 ? y[j] : 0.0;
-        for (int i = j + 1 + lane; i < n; i += 32) w = fma(__ldg(vj + i), y[i], w);
-        w = warp_sum(w) * tj;
-        if (lane == 0) y[j] -= w;
-        for (int i = j + 1 + lane; i < n; i += 32) y[i] = fma(-w, __ldg(vj + i), y[i]);
-        __syncwarp();
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int i = lo + lane;
+    for (; i + 96 < hi; i += 128) {
+        s0 = fma(a[i], b[i], s0);
+        s1 = fma(a[i + 32], b[i + 32], s1);
+        s2 = fma(a[i + 64], b[i + 64], s2);
+        s3 = fma(a[i + 96], b[i + 96], s3);
+    }
+    for (; i < hi; i += 32) s0 = fma(a[i], b[i], s0);
+    return warp_sum((s0 + s1) + (s2 + s3));
+}
+
+// Stage vector src[lo..hi) into dst[lo..hi) (whole CTA), using per-thread
+// prefetch registers: pre[q] holds src[lo + threadIdx.x + q*blockDim.x].
+constexpr int PRE = 8;   // supports n <= PRE * blockDim.x = 2048
+
+__device__ __forceinline__ void prefetch_vec(const double* __restrict__ src, int lo, int hi, double (&pre)[PRE]) {
+#pragma unroll
+    for (int q = 0; q < PRE; ++q) {
+        const int i = lo + threadIdx.x + q * blockDim.x;
+        pre[q] = (i < hi) ? __ldg(src + i) : 0.0;
+    }
+}
+__device__ __forceinline__ void store_vec(double* dst, int lo, int hi, const double (&pre)[PRE]) {
+#pragma unroll
+    for (int q = 0; q < PRE; ++q) {
+        const int i = lo + threadIdx.x + q * blockDim.x;
+        if (i < hi) dst[i] = pre[q];
     }
 }
 
-// Form column c of Q = H_0 ... H_{n-2} (Qt row c), multiplied by sgn[c]:
-// start from e_c, apply H_j for j = min(c, n-2) down to 0.  One warp per column.
+// Apply Q^T = H_{n-2} ... H_0 (H_0 first) to every column of Y (Yt rows).
+__global__ void __launch_bounds__(256) k_apply_qt(const double* __restrict__ Vt, const double* __restrict__ tau,
+                                                  double* Yt, int n, int ncols) {
+    extern __shared__ double cs_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = blockIdx.x * CPB;
+    double* vbuf = cs_smem;                      // n
+    double* col = cs_smem + n + (size_t)warp * n;
+    const int c = c0 + warp;
+    const bool has = c < ncols;
+    for (int w = 0; w < CPB; ++w)
+        if (c0 + w < ncols)
+            for (int i = threadIdx.x; i < n; i += blockDim.x) cs_smem[n + (size_t)w * n + i] = Yt[(size_t)(c0 + w) * n + i];
+    double pre[PRE];
+    prefetch_vec(Vt, 1, n, pre);                 // v_0 below the diagonal
+    for (int j = 0; j < n - 1; ++j) {
+        __syncthreads();
+        store_vec(vbuf, j + 1, n, pre);
+        if (threadIdx.x == 0) vbuf[j] = 1.0;
+        __syncthreads();
+        if (j + 1 < n - 1) prefetch_vec(Vt + (size_t)(j + 1) * n, j + 2, n, pre);
+        const double tj = __ldg(tau + j);
+        if (has && tj != 0.0) {
+            const double w = dot4(vbuf, col, j, n) * tj;
+            for (int i = j + lane; i < n; i += 32) col[i] = fma(-w, vbuf[i], col[i]);
+        }
+    }
+    __syncthreads();
+    for (int w = 0; w < CPB; ++w)
+        if (c0 + w < ncols)
+            for (int i = threadIdx.x; i < n; i += blockDim.x) Yt[(size_t)(c0 + w) * n + i] = cs_smem[n + (size_t)w * n + i];
+}
+
+// Form columns of Q = H_0 ... H_{n-2} (Qt rows), each multiplied by sgn[c]:
+// column c starts as e_c and takes H_j for j = min(c, n-2) down to 0.
 __global__ void __launch_bounds__(256) k_form_q(const double* __restrict__ Vt, const double* __restrict__ tau,
                                                 const double* __restrict__ sgn, double* Qt, int n) {
-    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (c >= n) return;
-    double* q = Qt + (size_t)c * n;
-    for (int i = lane; i < n; i += 32) q[i] = (i == c) ? 1.0 : 0.0;
-    __syncwarp();
-    for (int j = min(c, n - 2); j >= 0; --j) {
+    extern __shared__ double cs_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = blockIdx.x * CPB;
+    double* vbuf = cs_smem;
+    double* col = cs_smem + n + (size_t)warp * n;
+    const int c = c0 + warp;
+    const bool has = c < n;
+    for (int i = lane; i < n; i += 32) col[i] = (i == c) ? 1.0 : 0.0;
+    const int jtop = min(c0 + CPB - 1, n - 2);
+    double pre[PRE];
+    if (jtop >= 0) prefetch_vec(Vt + (size_t)jtop * n, jtop + 1, n, pre);
+    for (int j = jtop; j >= 0; --j) {
+        __syncthreads();
+        store_vec(vbuf, j + 1, n, pre);
+        if (threadIdx.x == 0) vbuf[j] = 1.0;
+        __syncthreads();
+        if (j > 0) prefetch_vec(Vt + (size_t)(j - 1) * n, j, n, pre);
         const double tj = __ldg(tau + j);
-        if (tj == 0.0) continue;
-        const double* vj = Vt + (size_t)j * n;
-        double w = lane == 0 ? q[j] : 0.0;
-        for (int i = j + 1 + lane; i < n; i += 32) w = fma(__ldg(vj + i), q[i], w);
-        w = warp_sum(w) * tj;
-        if (lane == 0) q[j] -= w;
-        for (int i = j + 1 + lane; i < n; i += 32) q[i] = fma(-w, __ldg(vj + i), q[i]);
-        __syncwarp();
+        if (has && j <= c && tj != 0.0) {
+            const double w = dot4(vbuf, col, j, n) * tj;
+            for (int i = j + lane; i < n; i += 32) col[i] = fma(-w, vbuf[i], col[i]);
+        }
     }
-    const double s = sgn[c];
-    for (int i = lane; i < n; i += 32) q[i] *= s;
+    __syncthreads();
+    if (has) {
+        const double s = sgn[c];
+        for (int i = lane; i < n; i += 32) Qt[(size_t)c * n + i] = col[i] * s;
+    }
 }
 
 // Back substitution: for every column y (row of Yt), solve R x = y with R the
 // upper triangle of the column-major Rt (R[i][c] = Rt[c][i]); writes
-// x_i * (xs ? 1/xs[i] : 1) into Xt.  One warp per column.
+// x_i * (xs ? 1/xs[i] : 1) into Xt.
 __global__ void __launch_bounds__(256) k_backsolve(const double* __restrict__ Rt, const double* __restrict__ Yt,
                                                    double* Xt, int n, int ncols, const double* xs, DevStatus* st) {
-    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (c >= ncols) return;
-    const double* y = Yt + (size_t)c * n;
-    double* x = Xt + (size_t)c * n;
-    for (int i = lane; i < n; i += 32) x[i] = y[i];
-    __syncwarp();
+    extern __shared__ double cs_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = blockIdx.x * CPB;
+    double* rbuf = cs_smem;                      // column i of R, rows 0..i
+    double* x = cs_smem + n + (size_t)warp * n;
+    double* rinv = cs_smem + (size_t)(CPB + 1) * n;   // 1 / R_ii
+    const int c = c0 + warp;
+    const bool has = c < ncols;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) rinv[i] = 1.0 / __ldg(Rt + (size_t)i * n + i);
+    if (has)
+        for (int i = lane; i < n; i += 32) x[i] = Yt[(size_t)c * n + i];
+    double pre[PRE];
+    prefetch_vec(Rt + (size_t)(n - 1) * n, 0, n, pre);
     for (int i = n - 1; i >= 0; --i) {
-        const double* ri = Rt + (size_t)i * n;
-        const double xi = x[i] / __ldg(ri + i);
-        __syncwarp();
-        if (lane == 0) x[i] = xi;
-        for (int r = lane; r < i; r += 32) x[r] = fma(-__ldg(ri + r), xi, x[r]);
-        __syncwarp();
+        __syncthreads();
+        store_vec(rbuf, 0, i + 1, pre);
+        __syncthreads();
+        if (i > 0) prefetch_vec(Rt + (size_t)(i - 1) * n, 0, i, pre);
+        if (has) {
+            const double xi = x[i] * rinv[i];
+            __syncwarp();
+            if (lane == 0) x[i] = xi;
+            for (int r = lane; r < i; r += 32) x[r] = fma(-rbuf[r], xi, x[r]);
+            __syncwarp();
+        }
     }
-    bool bad = false;
-    for (int i = lane; i < n; i += 32) {
-        double v = x[i];
-        if (xs) v /= xs[i];
-        if (!isfinite(v)) bad = true;
-        x[i] = v;
+    if (has) {
+        bool bad = false;
+        for (int i = lane; i < n; i += 32) {
+            double v = x[i];
+            if (xs) v /= xs[i];
+            if (!isfinite(v)) bad = true;
+            Xt[(size_t)c * n + i] = v;
+        }
+        if (__any_sync(0xffffffffu, bad) && lane == 0) flag_error(st, DERR_NUMERIC, 102);
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) flag_error(st, DERR_NUMERIC, 102);
 }
 
 // Column norms w_c = D_c * ||A_c|| of a column-major A (At); one warp per column.

@@ -93,6 +93,15 @@ __device__ void flush_tile_tf32(const UpdArgs& a, int k, int i0, int j0, uint32_
     const int g = lane >> 2, t = lane & 3;
     const int r0 = 16 * (warp >> 1);          // 4 row blocks of 16
     const int c0 = 32 * (warp & 1);           // 2 column blocks of 32 (4 n8 tiles)
+    // this thread's 16 entries of G, loaded before the tensor-core work
+    double gv[4][4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int row = i0 + r0 + g + 8 * (q >> 1), col = j0 + c0 + 8 * n + 2 * t + (q & 1);
+            gv[n][q] = (row < N && col < N) ? __ldcg(a.G + (size_t)row * N + col) : 0.0;
+        }
     float acc[4][4];
 #pragma unroll
     for (int n = 0; n < 4; ++n)
@@ -113,33 +122,182 @@ __device__ void flush_tile_tf32(const UpdArgs& a, int k, int i0, int j0, uint32_
         }
     }
 #pragma unroll
-    for (int n = 0; n < 4; ++n) {
-        const int col = j0 + c0 + 8 * n + 2 * t;
+    for (int n = 0; n < 4; ++n)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int row = i0 + r0 + g + 8 * h;
-            if (row >= N) continue;
-            double* gp = a.G + (size_t)row * N + col;
-            if (col < N) gp[0] = __ldcg(gp) - (double)acc[n][2 * h];
-            if (col + 1 < N) gp[1] = __ldcg(gp + 1) - (double)acc[n][2 * h + 1];
+        for (int q = 0; q < 4; ++q) {
+            const int row = i0 + r0 + g + 8 * (q >> 1), col = j0 + c0 + 8 * n + 2 * t + (q & 1);
+            if (row < N && col < N) a.G[(size_t)row * N + col] = gv[n][q] - (double)acc[n][q];
+        }
+}
+
+// ---------------------------------------------------------------------------
+// Split-TF32 flush tile on the 5th-generation tensor cores (tcgen05): one
+// 128 x 128 tile of G per CTA iteration, accumulator in tensor memory (TMEM,
+// 128 columns allocated per CTA for the kernel's lifetime), operands staged in
+// shared memory in the canonical no-swizzle K-major layout (core matrices of
+// 8 rows x 16 bytes; 16-byte steps along K inside a core matrix row, LBO =
+// 128 B between the two K-adjacent core matrices of one MMA, SBO = kp*32 B
+// between 8-row groups), 3 x kp/8 MMAs of m128n128k8 issued by one thread,
+// completion signalled by tcgen05.commit on an mbarrier.
+// Shared memory: 4 operands x 128 x kp x 4 B (128 KB at kp = 64).
+// ---------------------------------------------------------------------------
+constexpr int TCT = 128;                  // tile edge
+constexpr uint32_t IDESC_TF32_128x128 =   // kind::tf32 instruction descriptor
+    (1u << 4)                             // D format: F32
+    | (2u << 7) | (2u << 10)              // A, B format: TF32
+    | ((uint32_t)(TCT >> 3) << 17)        // N / 8
+    | ((uint32_t)(TCT >> 4) << 24);       // M / 16
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+        :: "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(IDESC_TF32_128x128), "r"(acc));
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase) {
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(mbar), "r"(phase) : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
+    }
+}
+
+// element (r, m) of a 128 x kp operand, byte offset in the canonical layout
+__device__ __forceinline__ uint32_t tc_off(int r, int m, int kp) {
+    return (uint32_t)((r >> 3) * (kp * 32) + (m >> 2) * 128 + (r & 7) * 16 + (m & 3) * 4);
+}
+
+// returns false on a wait timeout (error flagged)
+__device__ bool flush_tile_tcgen05(const UpdArgs& a, int k, int i0, int j0, unsigned char* sm, uint32_t tmem,
+                                   uint32_t mbar, uint32_t& phase) {
+    const int N = a.N;
+    const int kp = (k + 7) & ~7;
+    const uint32_t opb = (uint32_t)(TCT * kp * 4);       // bytes per operand
+    unsigned char* Ah = sm;
+    unsigned char* Al = sm + opb;
+    unsigned char* Bh = sm + 2 * opb;
+    unsigned char* Bl = sm + 3 * opb;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    for (int o = threadIdx.x; o < kp * TCT; o += blockDim.x) {
+        const int m = o / TCT, r = o - m * TCT;
+        double xv = 0.0, yv = 0.0;
+        if (m < k) {
+            if (i0 + r < N) xv = __ldcg(a.Xs + (size_t)m * N + i0 + r);
+            if (j0 + r < N) yv = __ldcg(a.Ys + (size_t)m * N + j0 + r);
+        }
+        const float xf = (float)xv, yf = (float)yv;
+        const uint32_t xhi = f32_to_tf32(xf), yhi = f32_to_tf32(yf);
+        const uint32_t off = tc_off(r, m, kp);
+        *reinterpret_cast<uint32_t*>(Ah + off) = xhi;
+        *reinterpret_cast<uint32_t*>(Al + off) = f32_to_tf32(xf - __uint_as_float(xhi));
+        *reinterpret_cast<uint32_t*>(Bh + off) = yhi;
+        *reinterpret_cast<uint32_t*>(Bl + off) = f32_to_tf32(yf - __uint_as_float(yhi));
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sbo = (uint32_t)(kp * 32);
+        const uint32_t ah = smem_u32(Ah), al = smem_u32(Al), bh = smem_u32(Bh), bl = smem_u32(Bl);
+        uint32_t acc = 0;
+        for (int s = 0; s < kp / 8; ++s) {
+            const uint32_t ko = (uint32_t)(s * 256);
+            tc_mma_tf32(tmem, tc_desc(al + ko, 128, sbo), tc_desc(bh + ko, 128, sbo), acc); acc = 1;
+            tc_mma_tf32(tmem, tc_desc(ah + ko, 128, sbo), tc_desc(bl + ko, 128, sbo), 1);
+            tc_mma_tf32(tmem, tc_desc(ah + ko, 128, sbo), tc_desc(bh + ko, 128, sbo), 1);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(mbar) : "memory");
+    }
+    const bool ok = mbar_wait_bounded(mbar, phase);
+    phase ^= 1u;
+    if (!ok) { flag_error(a.st, DERR_TIMEOUT, 210); return false; }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // warps w and w+4 share TMEM lanes 32*(w%4)..+31; they split the 128 columns
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = 32 * (warp & 3) + lane;
+    const int cbase = 64 * (warp >> 2);
+    for (int cc = 0; cc < 64; cc += 32) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(cbase + cc);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int gi = i0 + row;
+        if (gi < N) {
+            double* gp = a.G + (size_t)gi * N + j0 + cbase + cc;
+            const int lim = min(32, N - (j0 + cbase + cc));
+            double gv[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) gv[q] = (q < lim) ? __ldcg(gp + q) : 0.0;
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                if (q < lim) gp[q] = gv[q] - (double)__uint_as_float(v[q]);
         }
     }
+    return true;
 }
 
 __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
     extern __shared__ double upd_smem[];
-    __shared__ int s_dec[4];
-    __shared__ double s_coef;
     const int N = a.N, W = a.W, nd = a.nd;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int gthreads = gridDim.x * blockDim.x;
+    // tensor-memory accumulator and completion barrier of the tcgen05 flush
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar;
+    uint32_t tmem = 0, mbar = 0, phase = 0;
+    if (a.precision == 2) {
+        if (threadIdx.x < 32) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                         :: "r"(smem_u32(&s_tmem)), "r"(TCT) : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&s_mbar)), "r"(1) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tmem = s_tmem;
+        mbar = smem_u32(&s_mbar);
+    }
     int cursor = 0, k = 0;
     for (;;) {
         // ------------------------------------------------------------ phase B
+        // Thread 0 walks the window's sites and decides each one; the CTA syncs
+        // only at accepted sites.  Warp 0 keeps the diagonal of the window block
+        // current (one entry per lane, W <= 32; it is all the next decisions
+        // read), the other warps update the off-diagonal part of the trailing block.
         if (blockIdx.x == 0) {
             double* Gw = upd_smem;                        // W x (W+1)
-            double* uu = Gw + W * (W + 1);                // W uniforms
-            int8_t* sw = reinterpret_cast<int8_t*>(uu + W); // W field values
+            double* vv = Gw + W * (W + 1);                // W thresholds on r^2: u e^{-2 gamma s}
+            double* dd = vv + W;                          // W values of Delta
+            int8_t* sw = reinterpret_cast<int8_t*>(dd + W); // W field values
+            __shared__ int s_found[2];
+            __shared__ double s_c[2];
             const int nw = min(W, N - cursor);
             const int ld = W + 1;
             for (int o = threadIdx.x; o < nw * nw; o += blockDim.x) {
@@ -148,49 +306,66 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                                           : __ldcg(a.Gw + r * W + c);
             }
             for (int t = threadIdx.x; t < nw; t += blockDim.x) {
-                uu[t] = sm64_uniform(a.key, a.ctr0 + cursor + t);
-                sw[t] = a.s[cursor + t];
+                const int sg = a.s[cursor + t];
+                const double u = sm64_uniform(a.key, a.ctr0 + cursor + t);
+                // accept iff u < e^{2 gamma s} r^2  <=>  r^2 > u e^{-2 gamma s}
+                vv[t] = u * (sg > 0 ? a.ef_m : a.ef_p);
+                dd[t] = sg > 0 ? a.dl_p : a.dl_m;
+                sw[t] = (int8_t)sg;
             }
             __syncthreads();
-            int kk = k, tstop = nw;
-            for (int t = 0; t < nw; ++t) {
+            int kk = k, tstop = nw, t0 = 0, it = 0;
+            for (;; ++it) {
+                const int slot = it & 1;
                 if (threadIdx.x == 0) {
-                    const int i = cursor + t;
-                    const int sg = sw[t];
-                    const double g = Gw[t * ld + t];
-                    const double dl = sg > 0 ? a.dl_p : a.dl_m;
-                    const double ef = sg > 0 ? a.ef_p : a.ef_m;
-                    const double r = fma(dl, 1.0 - g, 1.0);
-                    const double R = ef * r * r;
-                    int acc = uu[t] < R;
-                    if (!isfinite(r)) { flag_error(a.st, DERR_NUMERIC, 200); acc = 0; }
-                    s_dec[0] = acc;
-                    if (acc) {
-                        s_coef = dl / r;
-                        a.msite[kk] = i;
-                        a.mcoef[kk] = dl / r;
-                        a.s[i] = (int8_t)(-sg);
+                    int found = -1;
+                    double c = 0.0;
+                    for (; t0 < nw; ++t0) {
+                        const double dl = dd[t0];
+                        const double r = fma(-dl, Gw[t0 * ld + t0], 1.0 + dl);   // 1 + Delta (1 - G_ii)
+                        if (!isfinite(r)) { flag_error(a.st, DERR_NUMERIC, 200); continue; }
+                        if (r * r > vv[t0]) {
+                            // c = Delta / r: FP32 reciprocal seed + two Newton steps in FP64
+                            double y = (double)__frcp_rn((float)r);
+                            y = fma(y, fma(-r, y, 1.0), y);
+                            y = fma(y, fma(-r, y, 1.0), y);
+                            found = t0;
+                            c = dl * y;
+                            break;
+                        }
                     }
+                    if (found >= 0) {
+                        a.msite[kk] = cursor + found;
+                        a.mcoef[kk] = c;
+                        a.s[cursor + found] = (int8_t)(-sw[found]);
+                        ++t0;
+                    }
+                    s_found[slot] = found;
+                    s_c[slot] = c;
                 }
                 __syncthreads();
-                if (s_dec[0]) {
-                    const double c = s_coef;
-                    const int rest = nw - t - 1;
-                    // x, y of the new move at the later window positions
-                    for (int p = threadIdx.x; p < rest; p += blockDim.x) {
-                        const int q = t + 1 + p;
-                        a.xw[kk * W + q] = c * Gw[q * ld + t];
-                        a.yw[kk * W + q] = -Gw[t * ld + q];
-                    }
-                    // rank-1 update of the trailing block: Gw -= x y^T
-                    for (int o = threadIdx.x; o < rest * rest; o += blockDim.x) {
-                        const int q = t + 1 + o / rest, p = t + 1 + o % rest;
-                        Gw[q * ld + p] = fma(c * Gw[q * ld + t], Gw[t * ld + p], Gw[q * ld + p]);
-                    }
-                    ++kk;
-                    __syncthreads();
-                    if (kk == nd) { tstop = t + 1; break; }
+                const int tf = s_found[slot];
+                if (tf < 0) break;
+                const double c = s_c[slot];
+                const int rest = nw - tf - 1;
+                for (int p = (int)threadIdx.x - 32; p >= 0 && p < rest; p += blockDim.x - 32) {
+                    const int q = tf + 1 + p;
+                    a.xw[kk * W + q] = c * Gw[q * ld + tf];
+                    a.yw[kk * W + q] = -Gw[tf * ld + q];
                 }
+                if (threadIdx.x < 32) {
+                    // warp 0: one diagonal entry per lane, then hand back to thread 0
+                    const int q = tf + 1 + (int)threadIdx.x;
+                    if (q < nw) Gw[q * ld + q] = fma(c * Gw[q * ld + tf], Gw[tf * ld + q], Gw[q * ld + q]);
+                    __syncwarp();
+                } else {
+                    for (int o = threadIdx.x - 32; o < rest * rest; o += blockDim.x - 32) {
+                        const int q = tf + 1 + o / rest, p = tf + 1 + o % rest;
+                        if (q != p) Gw[q * ld + p] = fma(c * Gw[q * ld + tf], Gw[tf * ld + p], Gw[q * ld + p]);
+                    }
+                }
+                ++kk;
+                if (kk == nd) { tstop = tf + 1; break; }
             }
             if (threadIdx.x == 0) {
                 a.ctl[0] = cursor;
@@ -200,48 +375,98 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                 if (kk > k) atomicAdd(a.n_acc, (unsigned long long)(kk - k));
             }
         }
-        if (!grid_barrier(a.st, 1)) return;
+        if (!grid_barrier(a.st, 1)) break;
         const int c0 = __ldcg(a.ctl + 0), kb = __ldcg(a.ctl + 1), ka = __ldcg(a.ctl + 2), c1 = __ldcg(a.ctl + 3);
         // ------------------------------------------------------------ phase C
-        // One warp per vector index j (spread over all CTAs); lane m owns the
-        // window's m-th new move, so no FP64 cross-lane reductions are needed.
+        // CTA b owns the contiguous vector indices [b*JPB, (b+1)*JPB), one warp
+        // per index, one lane per new move of the window (no FP64 cross-lane
+        // reductions).  Everything the loops read is first staged in shared
+        // memory: X, Y of the pending moves at the CTA's indices and at the
+        // window's sites, and the window tables of the new moves.
         if (ka > kb) {
             const int nn = ka - kb;
+            const int nw = c1 > c0 ? min(W, N - c0) : 0;
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+            const int JPB = (N + gridDim.x - 1) / gridDim.x;
+            const int jb = blockIdx.x * JPB;
+            const int nj = max(0, min(JPB, N - jb));
+            double* sXj = upd_smem;                  // kb x JPB
+            double* sYj = sXj + kb * JPB;            // kb x JPB
+            double* sXw = sYj + kb * JPB;            // kb x W  (X at the window sites)
+            double* sYw = sXw + kb * W;              // kb x W
+            double* sxw = sYw + kb * W;              // nn x W  (new moves' x at window positions)
+            double* syw = sxw + nn * W;              // nn x W
+            if (nj > 0) {
+                // issue all loads of a thread before its shared-memory stores
+                // (the loads are independent; one L2 latency instead of many)
+                constexpr int BATCH = 8;
+                const int n1 = kb * JPB, n2 = kb * W, n3 = nn * W;
+                const int tot = 2 * (n1 + n2 + n3);
+                for (int o0 = threadIdx.x; o0 < tot; o0 += BATCH * blockDim.x) {
+                    double v[BATCH];
+                    int dst[BATCH];
+#pragma unroll
+                    for (int q = 0; q < BATCH; ++q) {
+                        const int o = o0 + q * blockDim.x;
+                        dst[q] = -1;
+                        v[q] = 0.0;
+                        if (o >= tot) continue;
+                        const int half = o & 1, e = o >> 1;      // even: X, odd: Y
+                        const double* srcm = half ? a.Ys : a.Xs;
+                        if (e < n1) {
+                            const int p = e / JPB, jj = e - p * JPB;
+                            if (jj < nj) v[q] = __ldcg(srcm + (size_t)p * N + jb + jj);
+                            dst[q] = (half ? (int)(sYj - upd_smem) : (int)(sXj - upd_smem)) + e;
+                        } else if (e < n1 + n2) {
+                            const int f = e - n1, p = f / W, t = f - p * W;
+                            if (t < nw) v[q] = __ldcg(srcm + (size_t)p * N + c0 + t);
+                            dst[q] = (half ? (int)(sYw - upd_smem) : (int)(sXw - upd_smem)) + f;
+                        } else {
+                            const int f = e - n1 - n2;
+                            v[q] = __ldcg((half ? a.yw : a.xw) + kb * W + f);
+                            dst[q] = (half ? (int)(syw - upd_smem) : (int)(sxw - upd_smem)) + f;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < BATCH; ++q)
+                        if (dst[q] >= 0) upd_smem[dst[q]] = v[q];
+                }
+            }
+            __syncthreads();
             const bool mine = lane < nn;
             const int mm = kb + lane;
-            const int im = mine ? __ldcg(a.msite + mm) : 0;
+            const int im = mine ? __ldcg(a.msite + mm) : c0;
             const int tm = im - c0;
             const double cm = mine ? __ldcg(a.mcoef + mm) : 0.0;
-            for (int j = blockIdx.x + gridDim.x * warp; j < N; j += gridDim.x * nwarp) {
-                // contributions of moves pending from earlier windows (4 partial sums for ILP)
+            for (int jj = warp; jj < nj; jj += nwarp) {
+                const int j = jb + jj;
+                const double g_jm = mine ? __ldcg(a.G + (size_t)j * N + im) : 0.0;
+                const double g_mj = mine ? __ldcg(a.G + (size_t)im * N + j) : 0.0;
                 double ox0 = 0.0, ox1 = 0.0, oy0 = 0.0, oy1 = 0.0;
                 if (mine) {
                     int p = 0;
                     for (; p + 1 < kb; p += 2) {
-                        const double* X0 = a.Xs + (size_t)p * N;
-                        const double* Y0 = a.Ys + (size_t)p * N;
-                        ox0 = fma(__ldcg(X0 + j), __ldcg(Y0 + im), ox0);
-                        oy0 = fma(__ldcg(X0 + im), __ldcg(Y0 + j), oy0);
-                        ox1 = fma(__ldcg(X0 + N + j), __ldcg(Y0 + N + im), ox1);
-                        oy1 = fma(__ldcg(X0 + N + im), __ldcg(Y0 + N + j), oy1);
+                        ox0 = fma(sXj[p * JPB + jj], sYw[p * W + tm], ox0);
+                        oy0 = fma(sXw[p * W + tm], sYj[p * JPB + jj], oy0);
+                        ox1 = fma(sXj[(p + 1) * JPB + jj], sYw[(p + 1) * W + tm], ox1);
+                        oy1 = fma(sXw[(p + 1) * W + tm], sYj[(p + 1) * JPB + jj], oy1);
                     }
                     if (p < kb) {
-                        ox0 = fma(__ldcg(a.Xs + (size_t)p * N + j), __ldcg(a.Ys + (size_t)p * N + im), ox0);
-                        oy0 = fma(__ldcg(a.Xs + (size_t)p * N + im), __ldcg(a.Ys + (size_t)p * N + j), oy0);
+                        ox0 = fma(sXj[p * JPB + jj], sYw[p * W + tm], ox0);
+                        oy0 = fma(sXw[p * W + tm], sYj[p * JPB + jj], oy0);
                     }
                 }
                 // recursion over the new moves (Eq. DelayRgenk), lane m accumulates move m
-                double ax = mine ? __ldcg(a.G + (size_t)j * N + im) - (ox0 + ox1) : 0.0;
-                double ay = mine ? (j == im ? 1.0 : 0.0) - __ldcg(a.G + (size_t)im * N + j) + (oy0 + oy1) : 0.0;
+                double ax = mine ? g_jm - (ox0 + ox1) : 0.0;
+                double ay = mine ? (j == im ? 1.0 : 0.0) - g_mj + (oy0 + oy1) : 0.0;
                 double xv = 0.0, yv = 0.0;
                 for (int q = 0; q < nn; ++q) {
                     if (lane == q) { xv = cm * ax; yv = ay; }
                     const double xq = __shfl_sync(0xffffffffu, xv, q);
                     const double yq = __shfl_sync(0xffffffffu, yv, q);
                     if (mine && lane > q) {
-                        ax = fma(-xq, __ldcg(a.yw + (kb + q) * W + tm), ax);
-                        ay = fma(__ldcg(a.xw + (kb + q) * W + tm), yq, ay);
+                        ax = fma(-xq, syw[q * W + tm], ax);
+                        ay = fma(sxw[q * W + tm], yq, ay);
                     }
                 }
                 if (mine) {
@@ -250,12 +475,18 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                 }
             }
         }
-        if (!grid_barrier(a.st, 2)) return;
+        if (!grid_barrier(a.st, 2)) break;
         k = ka;
         const bool done = (c1 >= N);
         // ------------------------------------------------------------ phase F
         if (k > 0 && (k == nd || done)) {
-            if (a.precision == 1) {
+            if (a.precision == 2) {
+                const int nt = (N + TCT - 1) / TCT;
+                for (int tile = blockIdx.x; tile < nt * nt; tile += gridDim.x)
+                    if (!flush_tile_tcgen05(a, k, (tile / nt) * TCT, (tile % nt) * TCT,
+                                            reinterpret_cast<unsigned char*>(upd_smem), tmem, mbar, phase))
+                        break;
+            } else if (a.precision == 1) {
                 const int nt = (N + FT - 1) / FT;
                 for (int tile = blockIdx.x; tile < nt * nt; tile += gridDim.x)
                     flush_tile_tf32(a, k, (tile / nt) * FT, (tile % nt) * FT, reinterpret_cast<uint32_t*>(upd_smem));
@@ -288,9 +519,9 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                 }
             }
             k = 0;
-            if (!grid_barrier(a.st, 3)) return;
+            if (!grid_barrier(a.st, 3)) break;
         }
-        if (done) return;
+        if (done) break;
         cursor = c1;
         // ------------------------------------------------------------ phase A
         if (k > 0) {
@@ -305,8 +536,14 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                 acc = warp_sum(acc);
                 if (lane == 0) a.Gw[r * W + c] = __ldcg(a.G + (size_t)(cursor + r) * N + cursor + c) - acc;
             }
-            if (!grid_barrier(a.st, 4)) return;
+            if (!grid_barrier(a.st, 4)) break;
         }
+    }
+    if (a.precision == 2) {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x < 32)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TCT) : "memory");
     }
 }
 

@@ -10,19 +10,22 @@
 // B300 design: FP64 arithmetic is the bound (the measured DFMA rate is ~1/62 of
 // FP32), so the kernel minimises FP64 work: two real rows are packed into one
 // complex vector (the operator is real, E(a+ib) = Ea + iEb), each 1D DFT of
-// length n = a*b is one Cooley-Tukey split into two short naive passes, and the
-// whole pipeline for a row pair stays in shared memory (one HBM/L2 read and one
-// write per element).
+// length L is a mixed-radix Stockham FFT (radix 4, 2, 3 butterflies, a plain
+// small DFT for other primes such as 7), and the whole pipeline for a row pair
+// stays in shared memory (one L2/HBM read and one write per element).
 #pragma once
 #include "common.cuh"
 
 namespace afq {
 
+constexpr int FFT_MAX_STAGES = 8;
+
 struct FFTPlan {
     int N, Nc, L1, L2;
-    int a1, b1, a2, b2;          // L1 = a1*b1, L2 = a2*b2 (a <= b)
-    const double2* tw1;          // e^{-2 pi i m / L1}, m < L1
-    const double2* tw2;          // e^{-2 pi i m / L2}, m < L2
+    int nr1, nr2;                         // number of radix stages per dimension
+    int r1[FFT_MAX_STAGES], r2[FFT_MAX_STAGES];   // radices, product = L1 (L2)
+    const double2* tw1;                   // e^{-2 pi i m / L1}, m < L1
+    const double2* tw2;                   // e^{-2 pi i m / L2}, m < L2
 };
 
 // Diagonal scaling d_i = s_i > 0 ? vp : vm, or 1 when s == nullptr.
@@ -38,53 +41,81 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {   // a*b + c
     return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
 }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+// multiply by -i (forward) or +i (inverse)
+__device__ __forceinline__ double2 cmul_mi(double2 a, bool inverse) {
+    return inverse ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x);
+}
 
-// One naive DFT pass along dimension `dim` for all VP vectors and both
-// sublattices.  Output element at line position e (0..n-1) is
-//   mode 0 (full):   Y[e] = sum_{j<n} X[j] w^{j e}
-//   mode 1 (inner):  e = k1*b + j2:  Y[e] = w^{j2 k1} sum_{j1<a} X[j1*b + j2] w^{b j1 k1}
-//   mode 2 (outer):  e = k1 + a*k2:  Y[e] = sum_{j2<b} X[k1*b + j2] w^{a j2 k2}
-// with w = e^{-+2 pi i / n} (conj for the inverse).
-__device__ void dft_pass(const double2* __restrict__ src, double2* __restrict__ dst, int VP,
-                         const FFTPlan& P, int dim, int mode, bool inverse) {
+// One radix-R stage of a Stockham autosort FFT (Govindaraju et al., SC 2008)
+// along dimension `dim` for all VP vectors and both sublattices: butterfly j
+// (0 <= j < n/R) of a line reads R elements n/R apart, applies the twiddles
+// w^{r (j mod Ns) n/(Ns R)}, does an R-point DFT and writes them Ns apart from
+// (j / Ns) Ns R + j mod Ns.  w = e^{-2 pi i / n} (conjugate for the inverse).
+__device__ void fft_stage(const double2* __restrict__ src, double2* __restrict__ dst, int VP, const FFTPlan& P,
+                          int dim, int R, int Ns, bool inverse) {
     const int Nc = P.Nc, L1 = P.L1;
     const int n = dim == 1 ? P.L1 : P.L2;
-    const int a = dim == 1 ? P.a1 : P.a2;
-    const int b = dim == 1 ? P.b1 : P.b2;
     const double2* tw = dim == 1 ? P.tw1 : P.tw2;
     const double sg = inverse ? -1.0 : 1.0;
-    const int total = VP * 2 * Nc;
+    const int nb = n / R;                        // butterflies per line
+    const int lines = Nc / n;                    // lines per sublattice
+    const int total = VP * 2 * lines * nb;
+    const int tstep = n / (Ns * R);
     for (int o = threadIdx.x; o < total; o += blockDim.x) {
-        const int v = o / (2 * Nc);
-        const int rem = o - v * 2 * Nc;
-        const int sub = rem / Nc;
-        const int c = rem - sub * Nc;
-        int e, base, stride;
-        if (dim == 1) { e = c % L1; base = sub * Nc + (c - e); stride = 1; }
-        else          { e = c / L1; base = sub * Nc + (c - e * L1); stride = L1; }
+        const int j = o % nb;
+        const int rem = o / nb;
+        const int line = rem % lines;
+        const int vs = rem / lines;              // v * 2 + sub
+        const int v = vs >> 1, sub = vs & 1;
+        int base, stride;
+        if (dim == 1) { base = sub * Nc + line * L1; stride = 1; }
+        else          { base = sub * Nc + line;      stride = L1; }
         const double2* x = src + (size_t)v * P.N + base;
-        double2 acc = make_double2(0.0, 0.0);
-        if (mode == 0) {
-            for (int j = 0; j < n; ++j) {
-                double2 w = tw[(j * e) % n]; w.y *= sg;
-                acc = cfma(x[j * stride], w, acc);
+        double2* y = dst + (size_t)v * P.N + base;
+        const int jm = j % Ns;
+        const int od = (j / Ns) * Ns * R + jm;
+        double2 a[8];
+        for (int r = 0; r < R; ++r) {
+            double2 e = x[(j + r * nb) * stride];
+            if (r > 0 && jm > 0) {
+                double2 w = tw[(r * jm * tstep) % n];
+                w.y *= sg;
+                e = cmul(e, w);
             }
-        } else if (mode == 1) {
-            const int k1 = e / b, j2 = e - k1 * b;
-            for (int j1 = 0; j1 < a; ++j1) {
-                double2 w = tw[(b * j1 * k1) % n]; w.y *= sg;
-                acc = cfma(x[(j1 * b + j2) * stride], w, acc);
-            }
-            double2 w = tw[(j2 * k1) % n]; w.y *= sg;
-            acc = cmul(acc, w);
+            a[r] = e;
+        }
+        if (R == 2) {
+            y[od * stride] = cadd(a[0], a[1]);
+            y[(od + Ns) * stride] = csub(a[0], a[1]);
+        } else if (R == 4) {
+            const double2 s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
+            const double2 s13 = cadd(a[1], a[3]), d13 = cmul_mi(csub(a[1], a[3]), inverse);
+            y[od * stride] = cadd(s02, s13);
+            y[(od + Ns) * stride] = cadd(d02, d13);
+            y[(od + 2 * Ns) * stride] = csub(s02, s13);
+            y[(od + 3 * Ns) * stride] = csub(d02, d13);
+        } else if (R == 3) {
+            const double c3 = 0.86602540378443864676;       // sqrt(3)/2
+            const double2 t1 = cadd(a[1], a[2]), t2 = csub(a[1], a[2]);
+            const double2 m = make_double2(fma(-0.5, t1.x, a[0].x), fma(-0.5, t1.y, a[0].y));
+            const double2 it = cmul_mi(t2, inverse);        // -+ i t2
+            y[od * stride] = cadd(a[0], t1);
+            y[(od + Ns) * stride] = make_double2(fma(c3, it.x, m.x), fma(c3, it.y, m.y));
+            y[(od + 2 * Ns) * stride] = make_double2(fma(-c3, it.x, m.x), fma(-c3, it.y, m.y));
         } else {
-            const int k1 = e % a, k2 = e / a;
-            for (int j2 = 0; j2 < b; ++j2) {
-                double2 w = tw[(a * j2 * k2) % n]; w.y *= sg;
-                acc = cfma(x[(k1 * b + j2) * stride], w, acc);
+            // generic small radix: R-point DFT with roots from the same table
+            for (int q = 0; q < R; ++q) {
+                double2 acc = a[0];
+                for (int r = 1; r < R; ++r) {
+                    double2 w = tw[((q * r) % R) * nb];
+                    w.y *= sg;
+                    acc = cfma(a[r], w, acc);
+                }
+                y[(od + q * Ns) * stride] = acc;
             }
         }
-        dst[(size_t)v * P.N + sub * Nc + c] = acc;
     }
 }
 
@@ -94,16 +125,14 @@ __device__ double2* dft2d(double2* z, double2* t, int VP, const FFTPlan& P, bool
     double2* cur = z;
     double2* oth = t;
     for (int dim = 1; dim <= 2; ++dim) {
-        const int a = dim == 1 ? P.a1 : P.a2;
-        if (a == 1) {
-            dft_pass(cur, oth, VP, P, dim, 0, inverse);
+        const int ns = dim == 1 ? P.nr1 : P.nr2;
+        const int* rr = dim == 1 ? P.r1 : P.r2;
+        int Ns = 1;
+        for (int st = 0; st < ns; ++st) {
+            fft_stage(cur, oth, VP, P, dim, rr[st], Ns, inverse);
             __syncthreads();
-            double2* s = cur; cur = oth; oth = s;
-        } else {
-            dft_pass(cur, oth, VP, P, dim, 1, inverse);
-            __syncthreads();
-            dft_pass(oth, cur, VP, P, dim, 2, inverse);
-            __syncthreads();
+            Ns *= rr[st];
+            double2* sw = cur; cur = oth; oth = sw;
         }
     }
     return cur;

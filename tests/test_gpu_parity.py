@@ -178,3 +178,15 @@ def test_full_size_slice_parity(pkg):
     assert np.array_equal(ch.field()[0], oc.field[0])
     assert rel_err(Gg, oc.G) < TOL
     ch.close()
+
+
+def test_handles_of_different_sizes_coexist(pkg):
+    """Kernel shared-memory limits are process-wide: a handle created later with
+    smaller needs (smaller lattice, FP64 flush) must not break an earlier one."""
+    big = pkg.Chain(pkg.make_params(L=6, beta=1.0, dtau=0.1, U=3.73, n_delay=64, n_stab=5, seed=3, precision=1))
+    small = pkg.Chain(pkg.make_params(L=2, beta=1.0, dtau=0.1, U=3.73, n_delay=2, n_stab=5, seed=3, precision=0))
+    small.sweep(1)
+    st = big.sweep(1)
+    assert st.accepted > 0
+    small.close()
+    big.close()
