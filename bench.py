@@ -55,9 +55,12 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD_KEY, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
                     help="1: split-TF32 tensor-core flush (the L=24 precision workload); 0: plain FP64")
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 sweep")
+    ap.add_argument("--chains", type=int, default=2,
+                    help="independent chains per GPU, each on its own CUDA stream and host thread "
+                         "(2: any two of the cooperative kernels fit on one SM together)")
     return ap.parse_args()
 
 
@@ -232,17 +235,35 @@ def algorithmic_flops(family, N, Nc, accepted_per_update):
 
 
 def time_chain(pkg, torch, args, key, precision, rank, world, dev, dist, stream):
-    """Create one chain, run W warm-up sweeps, time K sweeps with CUDA events on
-    the library's stream (per-launch timing enabled).  Returns a result dict."""
+    """Create C chains (one CUDA stream and one host thread each), run W warm-up
+    sweeps, time K sweeps of every chain with CUDA events on the chains' streams
+    (per-launch timing enabled).  Returns a result dict (chain 0's observables)."""
+    import threading
     w, N, M = workload_config(key)
-    params = pkg.make_params(L=w["L"], beta=w["beta"], dtau=w["dtau"], U=w["U"], n_delay=w["n_delay"],
-                             n_stab=w["n_stab"], seed=1000 + rank, chain=rank, measure=1, device=dev,
-                             precision=precision)
-    ch = pkg.Chain(params, stream=stream.cuda_stream)
-    for _ in range(args.warmup):
-        ch.sweep(1)
-    ch.observables()
-    pkg.afqmc_set_timing(ch.h, 1)
+    C = max(1, args.chains)
+    streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(C - 1)]
+    chains = []
+    for c in range(C):
+        params = pkg.make_params(L=w["L"], beta=w["beta"], dtau=w["dtau"], U=w["U"], n_delay=w["n_delay"],
+                                 n_stab=w["n_stab"], seed=1000 + rank, chain=rank * C + c, measure=1,
+                                 device=dev, precision=precision)
+        chains.append(pkg.Chain(params, stream=streams[c].cuda_stream))
+    ch = chains[0]
+
+    def run_all(fn):
+        if C == 1:
+            fn(0)
+            return
+        ts = [threading.Thread(target=fn, args=(c,)) for c in range(C)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+
+    run_all(lambda c: chains[c].sweep(args.warmup))
+    for c in range(C):
+        chains[c].observables()
+        pkg.afqmc_set_timing(chains[c].h, 1)
 
     def barrier():
         if dist is not None:
@@ -252,24 +273,37 @@ def time_chain(pkg, torch, args, key, precision, rank, world, dev, dist, stream)
     clocks = ClockSampler(dev)
     barrier()
     clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    proposed = accepted = launches = 0
-    drift = 0.0
-    for _ in range(args.steps):
-        st = ch.sweep(1)
-        proposed += st.proposed
-        accepted += st.accepted
-        launches += st.launches
-        drift = max(drift, st.max_stab_drift)
-    e1.record(stream)
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(C)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(C)]
+    for c in range(C):
+        e0[c].record(streams[c])
+    stats = [[0, 0, 0, 0.0] for _ in range(C)]
+
+    def steps(c):
+        for _ in range(args.steps):
+            st = chains[c].sweep(1)
+            stats[c][0] += st.proposed
+            stats[c][1] += st.accepted
+            stats[c][2] += st.launches
+            stats[c][3] = max(stats[c][3], st.max_stab_drift)
+        e1[c].record(streams[c])
+
+    run_all(steps)
     barrier()
     ck = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    timing = pkg.afqmc_get_timing(ch.h)
-    pkg.afqmc_set_timing(ch.h, 0)
+    ms = max(e0[0].elapsed_time(e1[c]) for c in range(C))
+    proposed = sum(x[0] for x in stats)
+    accepted = sum(x[1] for x in stats)
+    launches = sum(x[2] for x in stats)
+    drift = max(x[3] for x in stats)
+    timing = None
+    for c in range(C):
+        t = pkg.afqmc_get_timing(chains[c].h)
+        pkg.afqmc_set_timing(chains[c].h, 0)
+        timing = t if timing is None else {k: (timing[k][0] + t[k][0], timing[k][1] + t[k][1]) for k in t}
     obs = ch.observables()
+    for c in range(1, C):
+        chains[c].observables()
     ms_max, total_proposed = ms, proposed
     if dist is not None:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
@@ -278,7 +312,7 @@ def time_chain(pkg, torch, args, key, precision, rank, world, dev, dist, stream)
         p = torch.tensor([float(proposed)], dtype=torch.float64, device=dev)
         dist.all_reduce(p, op=dist.ReduceOp.SUM)
         total_proposed = float(p.item())
-    return dict(chain=ch, ms=ms_max, value=total_proposed / (ms_max / 1e3), proposed=proposed,
+    return dict(chain=ch, chains=chains, run_all=run_all, ms=ms_max, value=total_proposed / (ms_max / 1e3), proposed=proposed,
                 total_proposed=total_proposed, accepted=accepted, launches=launches, drift=drift,
                 timing=timing, obs=obs, clocks=ck, barrier=barrier)
 
@@ -327,7 +361,8 @@ def run_ours(args):
     ref64 = None
     if args.precision != 0 and not args.no_fp64:
         ref64 = time_chain(pkg, torch, args, key, 0, rank, world, dev, dist, stream)
-        ref64["chain"].close()
+        for c in ref64["chains"]:
+            c.close()
     ch = head["chain"]
     barrier = head["barrier"]
 
@@ -335,16 +370,21 @@ def run_ours(args):
     # results back to host memory (observable averages and the field); state stays resident.
     e2e = None
     if not args.no_e2e:
-        nbytes = 0
+        nb = [0] * len(head["chains"])
+
+        def e2e_steps(c):
+            chn = head["chains"][c]
+            for _ in range(args.steps):
+                chn.sweep(1)
+                o = chn.observables()
+                f = chn.field()
+                nb[c] = 10 * 8 + o["Czz"].nbytes + o["nk"].nbytes + f.nbytes
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            ch.sweep(1)
-            o = ch.observables()
-            f = ch.field()
-            nbytes = 10 * 8 + o["Czz"].nbytes + o["nk"].nbytes + f.nbytes
+        head["run_all"](e2e_steps)
         barrier()
         wall = time.perf_counter() - t0
+        nbytes = sum(nb)
         e2e_val = head["proposed"] / wall
         if dist is not None:
             t = torch.tensor([wall], dtype=torch.float64, device=dev)
@@ -359,7 +399,7 @@ def run_ours(args):
            "data": "synthetic (random initial Ising field from the seed; no dataset)",
            "config": {"workload": key, "L": w["L"], "N_sites": N, "beta": w["beta"], "dtau": w["dtau"], "M": M,
                       "U": w["U"], "n_delay": w["n_delay"], "n_stab": w["n_stab"], "precision": args.precision,
-                      "chains_per_gpu": 1, "parallelism": f"replicas{world}",
+                      "chains_per_gpu": max(1, args.chains), "parallelism": f"replicas{world}",
                       "l2": "no flush: a sweep streams the UDT stacks (1.3 GB) through the 126 MB L2"},
            "roofline": roofline_of(head["timing"], N, head["accepted"], args.precision),
            "gpu_launches": int(head["launches"]),
@@ -380,7 +420,8 @@ def run_ours(args):
         out["clocks"] = head["clocks"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(key)
-    ch.close()
+    for c in head["chains"]:
+        c.close()
     if rank == 0:
         print(json.dumps(out))
     if dist is not None:

@@ -251,12 +251,14 @@ size_t cpb_smem(int n) { return sizeof(double) * (size_t)(CPB + 2) * n; }
 
 // dynamic shared memory of k_update_slice: window block (phase B) or flush tiles (phase F)
 size_t update_smem(int W, int nd, int precision, int N = AFQMC_NOALLOC_MAX_N, int grid = 148) {
-    size_t b = sizeof(double) * ((size_t)W * (W + 1) + 3 * W);
+    size_t b = sizeof(double) * ((size_t)W * (W + 1) + 4 * W);
     const size_t jpb = (size_t)((N + grid - 1) / grid);
     b = std::max(b, sizeof(double) * (2 * (size_t)nd * jpb + 2 * (size_t)nd * W + 2 * (size_t)W * W));   // phase C staging
     size_t f = sizeof(double) * 2 * (size_t)nd * 32;
-    if (precision == 1) f = std::max(f, sizeof(uint32_t) * 4 * (size_t)((nd + 7) & ~7) * FT);
-    if (precision == 2) f = std::max(f, sizeof(uint32_t) * 4 * (size_t)((nd + 7) & ~7) * TCT);
+    if (precision == 1) {
+        f = std::max(f, sizeof(uint32_t) * 4 * (size_t)TCK * TCT);     // TF32 operands of one K round
+        f = std::max(f, sizeof(float) * (size_t)TCT * (TCT + 1));      // accumulator tile
+    }
     return std::max(b, f);
 }
 
@@ -522,8 +524,7 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
     if (!(P.U >= 0)) return bad("U must be >= 0");
     if (P.theta1 != 0.0 || P.theta2 != 0.0) return bad("twisted boundaries are not supported in this version");
     if (P.hs_channel != 0) return bad("only the spin channel (hs_channel = 0) is supported");
-    if (P.precision < 0 || P.precision > 2) return bad("precision must be 0 (FP64) or 1 (split-TF32 flush)");
-    if (P.precision == 2 && P.n_delay > 64) return bad("the tcgen05 flush supports n_delay <= 64");
+    if (P.precision != 0 && P.precision != 1) return bad("precision must be 0 (FP64) or 1 (split-TF32 flush)");
     const double Mr = P.beta / P.dtau;
     const int M = (int)std::llround(Mr);
     if (M < 1 || std::fabs(M * P.dtau - P.beta) > 1e-9) return bad("beta must be an integer multiple of dtau");

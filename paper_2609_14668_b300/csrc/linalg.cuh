@@ -310,18 +310,22 @@ __global__ void __launch_bounds__(256) k_apply_qt(const double* __restrict__ Vt,
 }
 
 // Form columns of Q = H_0 ... H_{n-2} (Qt rows), each multiplied by sgn[c]:
-// column c starts as e_c and takes H_j for j = min(c, n-2) down to 0.
+// column c starts as e_c and takes H_j for j = min(c, n-2) down to 0.  Column c
+// needs about 2 c n FMAs, so the columns of a CTA are taken cyclically
+// (b, b + G, b + 2G, ...) to give every CTA the same mix of short and long ones.
 __global__ void __launch_bounds__(256) k_form_q(const double* __restrict__ Vt, const double* __restrict__ tau,
                                                 const double* __restrict__ sgn, double* Qt, int n) {
     extern __shared__ double cs_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c0 = blockIdx.x * CPB;
     double* vbuf = cs_smem;
     double* col = cs_smem + n + (size_t)warp * n;
-    const int c = c0 + warp;
+    const int c = blockIdx.x + gridDim.x * warp;
     const bool has = c < n;
     for (int i = lane; i < n; i += 32) col[i] = (i == c) ? 1.0 : 0.0;
-    const int jtop = min(c0 + CPB - 1, n - 2);
+    int cmax = blockIdx.x;
+    for (int w = 1; w < CPB; ++w)
+        if ((int)blockIdx.x + (int)gridDim.x * w < n) cmax = blockIdx.x + gridDim.x * w;
+    const int jtop = min(cmax, n - 2);
     double pre[PRE];
     if (jtop >= 0) prefetch_vec(Vt + (size_t)jtop * n, jtop + 1, n, pre);
     for (int j = jtop; j >= 0; --j) {

@@ -43,91 +43,19 @@ struct UpdArgs {
     uint64_t key, ctr0;           // random number of site i is u(key, ctr0 + i)
     unsigned long long* n_acc;
     DevStatus* st;
-    int precision;                // 0: FP64 flush; 1: split-TF32 tensor-core flush, FP32 accumulate
+    int precision;                // 0: FP64 flush; 1: split-TF32 tcgen05 flush, FP32 accumulate
 };
 
 // ---------------------------------------------------------------------------
-// Split-TF32 flush tile (precision 1): G[i0:i0+64, j0:j0+64] -= X Y with
-// X = Xh + Xl, Y = Yh + Yl (each part a TF32 number, from the FP32 rounding of
-// the FP64 value), product Xh Yh + Xh Yl + Xl Yh on the tensor cores with
-// FP32 accumulation (Ootomo & Yokota 2022), subtracted in FP64.
+// Split-TF32 flush (precision 1): G -= X Y with X = Xh + Xl, Y = Yh + Yl (each
+// part a TF32 number, from the FP32 rounding of the FP64 value), product
+// Xh Yh + Xh Yl + Xl Yh on the tensor cores with FP32 accumulation (Ootomo &
+// Yokota 2022), subtracted in FP64.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return r;
-}
-
-__device__ __forceinline__ void mma_m16n8k8_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-constexpr int FT = 64;   // flush tile edge (precision 1)
-
-// smem: 4 arrays of kp x FT uint32 (kp = k rounded up to 8): Xh, Xl, Yh, Yl.
-__device__ void flush_tile_tf32(const UpdArgs& a, int k, int i0, int j0, uint32_t* sm) {
-    const int N = a.N;
-    const int kp = (k + 7) & ~7;
-    uint32_t* xh = sm;
-    uint32_t* xl = xh + kp * FT;
-    uint32_t* yh = xl + kp * FT;
-    uint32_t* yl = yh + kp * FT;
-    __syncthreads();
-    for (int o = threadIdx.x; o < kp * FT; o += blockDim.x) {
-        const int m = o / FT, q = o - m * FT;
-        double xv = 0.0, yv = 0.0;
-        if (m < k) {
-            if (i0 + q < N) xv = __ldcg(a.Xs + (size_t)m * N + i0 + q);
-            if (j0 + q < N) yv = __ldcg(a.Ys + (size_t)m * N + j0 + q);
-        }
-        const float xf = (float)xv, yf = (float)yv;
-        const uint32_t xhi = f32_to_tf32(xf), yhi = f32_to_tf32(yf);
-        xh[o] = xhi; xl[o] = f32_to_tf32(xf - __uint_as_float(xhi));
-        yh[o] = yhi; yl[o] = f32_to_tf32(yf - __uint_as_float(yhi));
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    const int r0 = 16 * (warp >> 1);          // 4 row blocks of 16
-    const int c0 = 32 * (warp & 1);           // 2 column blocks of 32 (4 n8 tiles)
-    // this thread's 16 entries of G, loaded before the tensor-core work
-    double gv[4][4];
-#pragma unroll
-    for (int n = 0; n < 4; ++n)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int row = i0 + r0 + g + 8 * (q >> 1), col = j0 + c0 + 8 * n + 2 * t + (q & 1);
-            gv[n][q] = (row < N && col < N) ? __ldcg(a.G + (size_t)row * N + col) : 0.0;
-        }
-    float acc[4][4];
-#pragma unroll
-    for (int n = 0; n < 4; ++n)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[n][q] = 0.f;
-    for (int k0 = 0; k0 < kp; k0 += 8) {
-        const int ka = (k0 + t) * FT, kb = (k0 + t + 4) * FT;
-        const uint32_t ah[4] = {xh[ka + r0 + g], xh[ka + r0 + g + 8], xh[kb + r0 + g], xh[kb + r0 + g + 8]};
-        const uint32_t al[4] = {xl[ka + r0 + g], xl[ka + r0 + g + 8], xl[kb + r0 + g], xl[kb + r0 + g + 8]};
-#pragma unroll
-        for (int n = 0; n < 4; ++n) {
-            const int cc = c0 + 8 * n + g;
-            const uint32_t bh0 = yh[ka + cc], bh1 = yh[kb + cc];
-            const uint32_t bl0 = yl[ka + cc], bl1 = yl[kb + cc];
-            mma_m16n8k8_tf32(acc[n], al, bh0, bh1);
-            mma_m16n8k8_tf32(acc[n], ah, bl0, bl1);
-            mma_m16n8k8_tf32(acc[n], ah, bh0, bh1);
-        }
-    }
-#pragma unroll
-    for (int n = 0; n < 4; ++n)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int row = i0 + r0 + g + 8 * (q >> 1), col = j0 + c0 + 8 * n + 2 * t + (q & 1);
-            if (row < N && col < N) a.G[(size_t)row * N + col] = gv[n][q] - (double)acc[n][q];
-        }
 }
 
 // ---------------------------------------------------------------------------
@@ -139,7 +67,8 @@ __device__ void flush_tile_tf32(const UpdArgs& a, int k, int i0, int j0, uint32_
 // 128 B between the two K-adjacent core matrices of one MMA, SBO = kp*32 B
 // between 8-row groups), 3 x kp/8 MMAs of m128n128k8 issued by one thread,
 // completion signalled by tcgen05.commit on an mbarrier.
-// Shared memory: 4 operands x 128 x kp x 4 B (128 KB at kp = 64).
+// K is staged in rounds of 32 (shared memory: 4 operands x 128 x 32 x 4 B = 64 KB),
+// then the accumulator tile goes through shared memory (128 x 129 floats).
 // ---------------------------------------------------------------------------
 constexpr int TCT = 128;                  // tile edge
 constexpr uint32_t IDESC_TF32_128x128 =   // kind::tf32 instruction descriptor
@@ -179,57 +108,75 @@ __device__ __forceinline__ uint32_t tc_off(int r, int m, int kp) {
     return (uint32_t)((r >> 3) * (kp * 32) + (m >> 2) * 128 + (r & 7) * 16 + (m & 3) * 4);
 }
 
+constexpr int TCK = 32;                   // K staged per round (shared memory: 4 x 128 x 32 x 4 B = 64 KB)
+
 // returns false on a wait timeout (error flagged)
 __device__ bool flush_tile_tcgen05(const UpdArgs& a, int k, int i0, int j0, unsigned char* sm, uint32_t tmem,
                                    uint32_t mbar, uint32_t& phase) {
     const int N = a.N;
-    const int kp = (k + 7) & ~7;
-    const uint32_t opb = (uint32_t)(TCT * kp * 4);       // bytes per operand
     unsigned char* Ah = sm;
-    unsigned char* Al = sm + opb;
-    unsigned char* Bh = sm + 2 * opb;
-    unsigned char* Bl = sm + 3 * opb;
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    for (int o = threadIdx.x; o < kp * TCT; o += blockDim.x) {
-        const int m = o / TCT, r = o - m * TCT;
-        double xv = 0.0, yv = 0.0;
-        if (m < k) {
-            if (i0 + r < N) xv = __ldcg(a.Xs + (size_t)m * N + i0 + r);
-            if (j0 + r < N) yv = __ldcg(a.Ys + (size_t)m * N + j0 + r);
+    unsigned char* Al = sm + TCT * TCK * 4;
+    unsigned char* Bh = sm + 2 * TCT * TCK * 4;
+    unsigned char* Bl = sm + 3 * TCT * TCK * 4;
+    for (int k0 = 0; k0 < k; k0 += TCK) {
+        const int kc = min(TCK, k - k0);
+        const int kp = (kc + 7) & ~7;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        constexpr int SB = 8;
+        for (int o0 = threadIdx.x; o0 < kp * TCT; o0 += SB * blockDim.x) {
+            double xv[SB], yv[SB];
+#pragma unroll
+            for (int q = 0; q < SB; ++q) {
+                const int o = o0 + q * blockDim.x;
+                const int m = o / TCT, r = o - m * TCT;
+                const bool in = o < kp * TCT && m < kc;
+                xv[q] = (in && i0 + r < N) ? __ldcg(a.Xs + (size_t)(k0 + m) * N + i0 + r) : 0.0;
+                yv[q] = (in && j0 + r < N) ? __ldcg(a.Ys + (size_t)(k0 + m) * N + j0 + r) : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < SB; ++q) {
+                const int o = o0 + q * blockDim.x;
+                if (o >= kp * TCT) break;
+                const int m = o / TCT, r = o - m * TCT;
+                const float xf = (float)xv[q], yf = (float)yv[q];
+                const uint32_t xhi = f32_to_tf32(xf), yhi = f32_to_tf32(yf);
+                const uint32_t off = tc_off(r, m, kp);
+                *reinterpret_cast<uint32_t*>(Ah + off) = xhi;
+                *reinterpret_cast<uint32_t*>(Al + off) = f32_to_tf32(xf - __uint_as_float(xhi));
+                *reinterpret_cast<uint32_t*>(Bh + off) = yhi;
+                *reinterpret_cast<uint32_t*>(Bl + off) = f32_to_tf32(yf - __uint_as_float(yhi));
+            }
         }
-        const float xf = (float)xv, yf = (float)yv;
-        const uint32_t xhi = f32_to_tf32(xf), yhi = f32_to_tf32(yf);
-        const uint32_t off = tc_off(r, m, kp);
-        *reinterpret_cast<uint32_t*>(Ah + off) = xhi;
-        *reinterpret_cast<uint32_t*>(Al + off) = f32_to_tf32(xf - __uint_as_float(xhi));
-        *reinterpret_cast<uint32_t*>(Bh + off) = yhi;
-        *reinterpret_cast<uint32_t*>(Bl + off) = f32_to_tf32(yf - __uint_as_float(yhi));
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t sbo = (uint32_t)(kp * 32);
-        const uint32_t ah = smem_u32(Ah), al = smem_u32(Al), bh = smem_u32(Bh), bl = smem_u32(Bl);
-        uint32_t acc = 0;
-        for (int s = 0; s < kp / 8; ++s) {
-            const uint32_t ko = (uint32_t)(s * 256);
-            tc_mma_tf32(tmem, tc_desc(al + ko, 128, sbo), tc_desc(bh + ko, 128, sbo), acc); acc = 1;
-            tc_mma_tf32(tmem, tc_desc(ah + ko, 128, sbo), tc_desc(bl + ko, 128, sbo), 1);
-            tc_mma_tf32(tmem, tc_desc(ah + ko, 128, sbo), tc_desc(bh + ko, 128, sbo), 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sbo = (uint32_t)(kp * 32);
+            const uint32_t ah = smem_u32(Ah), al = smem_u32(Al), bh = smem_u32(Bh), bl = smem_u32(Bl);
+            uint32_t acc = k0 > 0 ? 1u : 0u;
+            for (int s = 0; s < kp / 8; ++s) {
+                const uint32_t ko = (uint32_t)(s * 256);
+                tc_mma_tf32(tmem, tc_desc(al + ko, 128, sbo), tc_desc(bh + ko, 128, sbo), acc); acc = 1;
+                tc_mma_tf32(tmem, tc_desc(ah + ko, 128, sbo), tc_desc(bl + ko, 128, sbo), 1);
+                tc_mma_tf32(tmem, tc_desc(ah + ko, 128, sbo), tc_desc(bh + ko, 128, sbo), 1);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(mbar) : "memory");
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     :: "r"(mbar) : "memory");
+        const bool ok = mbar_wait_bounded(mbar, phase);
+        phase ^= 1u;
+        if (!ok) { flag_error(a.st, DERR_TIMEOUT, 210); return false; }
     }
-    const bool ok = mbar_wait_bounded(mbar, phase);
-    phase ^= 1u;
-    if (!ok) { flag_error(a.st, DERR_TIMEOUT, 210); return false; }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // warps w and w+4 share TMEM lanes 32*(w%4)..+31; they split the 128 columns
+    // warps w and w+4 share TMEM lanes 32*(w%4)..+31; they split the 128 columns.
+    // The tile goes through shared memory (row-major, padded: conflict-free)
+    // so that G is then read and written in warp-contiguous row segments.
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = 32 * (warp & 3) + lane;
     const int cbase = 64 * (warp >> 2);
+    constexpr int CLD = TCT + 1;
+    float* ct = reinterpret_cast<float*>(sm);          // operands are consumed: reuse
     for (int cc = 0; cc < 64; cc += 32) {
         uint32_t v[32];
         const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(cbase + cc);
@@ -244,16 +191,24 @@ __device__ bool flush_tile_tcgen05(const UpdArgs& a, int k, int i0, int j0, unsi
               "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int gi = i0 + row;
-        if (gi < N) {
-            double* gp = a.G + (size_t)gi * N + j0 + cbase + cc;
-            const int lim = min(32, N - (j0 + cbase + cc));
-            double gv[32];
 #pragma unroll
-            for (int q = 0; q < 32; ++q) gv[q] = (q < lim) ? __ldcg(gp + q) : 0.0;
+        for (int q = 0; q < 32; ++q) ct[row * CLD + cbase + cc + q] = __uint_as_float(v[q]);
+    }
+    __syncthreads();
+    for (int r = warp; r < TCT; r += 8) {
+        const int gi = i0 + r;
+        if (gi >= N) break;
+        double* grow = a.G + (size_t)gi * N + j0;
+        double gv[TCT / 32];
 #pragma unroll
-            for (int q = 0; q < 32; ++q)
-                if (q < lim) gp[q] = gv[q] - (double)__uint_as_float(v[q]);
+        for (int q = 0; q < TCT / 32; ++q) {
+            const int c = lane + 32 * q;
+            gv[q] = (j0 + c < N) ? __ldcg(grow + c) : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < TCT / 32; ++q) {
+            const int c = lane + 32 * q;
+            if (j0 + c < N) grow[c] = gv[q] - (double)ct[r * CLD + c];
         }
     }
     return true;
@@ -268,7 +223,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_mbar;
     uint32_t tmem = 0, mbar = 0, phase = 0;
-    if (a.precision == 2) {
+    if (a.precision == 1) {
         if (threadIdx.x < 32) {
             asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                          :: "r"(smem_u32(&s_tmem)), "r"(TCT) : "memory");
@@ -295,7 +250,8 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
             double* Gw = upd_smem;                        // W x (W+1)
             double* vv = Gw + W * (W + 1);                // W thresholds on r^2: u e^{-2 gamma s}
             double* dd = vv + W;                          // W values of Delta
-            int8_t* sw = reinterpret_cast<int8_t*>(dd + W); // W field values
+            double* od = dd + W;                          // W values of 1 + Delta
+            int8_t* sw = reinterpret_cast<int8_t*>(od + W); // W field values
             __shared__ int s_found[2];
             __shared__ double s_c[2];
             const int nw = min(W, N - cursor);
@@ -311,6 +267,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                 // accept iff u < e^{2 gamma s} r^2  <=>  r^2 > u e^{-2 gamma s}
                 vv[t] = u * (sg > 0 ? a.ef_m : a.ef_p);
                 dd[t] = sg > 0 ? a.dl_p : a.dl_m;
+                od[t] = 1.0 + dd[t];
                 sw[t] = (int8_t)sg;
             }
             __syncthreads();
@@ -322,11 +279,12 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                     double c = 0.0;
                     for (; t0 < nw; ++t0) {
                         const double dl = dd[t0];
-                        const double r = fma(-dl, Gw[t0 * ld + t0], 1.0 + dl);   // 1 + Delta (1 - G_ii)
+                        const double r = fma(-dl, Gw[t0 * ld + t0], od[t0]);   // 1 + Delta (1 - G_ii)
                         if (!isfinite(r)) { flag_error(a.st, DERR_NUMERIC, 200); continue; }
                         if (r * r > vv[t0]) {
-                            // c = Delta / r: FP32 reciprocal seed + two Newton steps in FP64
-                            double y = (double)__frcp_rn((float)r);
+                            // c = Delta / r: hardware reciprocal estimate + two Newton steps
+                            double y;
+                            asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(r));
                             y = fma(y, fma(-r, y, 1.0), y);
                             y = fma(y, fma(-r, y, 1.0), y);
                             found = t0;
@@ -334,12 +292,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                             break;
                         }
                     }
-                    if (found >= 0) {
-                        a.msite[kk] = cursor + found;
-                        a.mcoef[kk] = c;
-                        a.s[cursor + found] = (int8_t)(-sw[found]);
-                        ++t0;
-                    }
+                    if (found >= 0) ++t0;
                     s_found[slot] = found;
                     s_c[slot] = c;
                 }
@@ -347,6 +300,11 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                 const int tf = s_found[slot];
                 if (tf < 0) break;
                 const double c = s_c[slot];
+                if (threadIdx.x == 32) {
+                    a.msite[kk] = cursor + tf;
+                    a.mcoef[kk] = c;
+                    a.s[cursor + tf] = (int8_t)(-sw[tf]);
+                }
                 const int rest = nw - tf - 1;
                 for (int p = (int)threadIdx.x - 32; p >= 0 && p < rest; p += blockDim.x - 32) {
                     const int q = tf + 1 + p;
@@ -480,16 +438,12 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
         const bool done = (c1 >= N);
         // ------------------------------------------------------------ phase F
         if (k > 0 && (k == nd || done)) {
-            if (a.precision == 2) {
+            if (a.precision == 1) {
                 const int nt = (N + TCT - 1) / TCT;
                 for (int tile = blockIdx.x; tile < nt * nt; tile += gridDim.x)
                     if (!flush_tile_tcgen05(a, k, (tile / nt) * TCT, (tile % nt) * TCT,
                                             reinterpret_cast<unsigned char*>(upd_smem), tmem, mbar, phase))
                         break;
-            } else if (a.precision == 1) {
-                const int nt = (N + FT - 1) / FT;
-                for (int tile = blockIdx.x; tile < nt * nt; tile += gridDim.x)
-                    flush_tile_tf32(a, k, (tile / nt) * FT, (tile % nt) * FT, reinterpret_cast<uint32_t*>(upd_smem));
             } else {
                 double* xs = upd_smem;               // k x 32
                 double* ys = upd_smem + nd * 32;     // k x 32
@@ -539,7 +493,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
             if (!grid_barrier(a.st, 4)) break;
         }
     }
-    if (a.precision == 2) {
+    if (a.precision == 1) {
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         if (threadIdx.x < 32)
