@@ -89,12 +89,13 @@ typedef struct {
 enum {
     AFQMC_K_PROPAGATE = 0,  /* momentum-space propagation rows (wrap, chain products, half step) */
     AFQMC_K_UPDATE = 1,     /* delayed-update slice kernel (proposals, x/y recursion, flush) */
-    AFQMC_K_QR = 2,         /* Householder QR */
+    AFQMC_K_QR = 2,         /* Householder QR of the stack products */
     AFQMC_K_GEMM = 3,       /* FP64 GEMM */
-    AFQMC_K_QRAUX = 4,      /* Q formation, Q^T application, back substitution, pivoting */
+    AFQMC_K_QRAUX = 4,      /* Q formation, pivoting, triangular solves of the middle matrix */
     AFQMC_K_MEASURE = 5,    /* observables */
     AFQMC_K_MISC = 6,       /* copies of identity, drift check, small helpers */
-    AFQMC_K_COUNT = 7
+    AFQMC_K_LU = 7,         /* LU with partial pivoting of the middle matrix of G */
+    AFQMC_K_COUNT = 8
 };
 typedef struct {
     uint64_t launches[AFQMC_K_COUNT];
@@ -168,10 +169,16 @@ afqmc_status afqmc_update_slice(afqmc_handle* h, int32_t slice, int32_t pass,
  * slice l recomputed from scratch. */
 afqmc_status afqmc_det_ratio(afqmc_handle* h, int32_t slice, int32_t site, double out[2]);
 
-/* Enable (1) or disable (0) per-launch CUDA-event timing; resets the totals. */
-afqmc_status afqmc_set_timing(afqmc_handle* h, int32_t enable);
+/* Per-launch CUDA-event timing of the kernel families whose bit (1 << AFQMC_K_*)
+ * is set in family_mask; 0 disables timing, AFQMC_TIMING_ALL times every
+ * family.  Resets the totals.  Each timed launch records two events on the
+ * handle's stream, so time only the families being studied when the
+ * surrounding throughput matters.  Bits above AFQMC_TIMING_ALL: AFQMC_E_INVALID. */
+#define AFQMC_TIMING_ALL ((1 << AFQMC_K_COUNT) - 1)
+afqmc_status afqmc_set_timing(afqmc_handle* h, int32_t family_mask);
 
-/* Totals since afqmc_set_timing (synchronises the stream). */
+/* Totals since afqmc_set_timing (synchronises the stream); the launch counts
+ * cover every family, the times only the timed ones (0 for the others). */
 afqmc_status afqmc_get_timing(afqmc_handle* h, afqmc_timing* out);
 
 /* Largest sizes accepted by afqmc_update_slice_noalloc. */

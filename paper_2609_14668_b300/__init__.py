@@ -36,11 +36,11 @@ class afqmc_sweep_stats(ctypes.Structure):
                 ("launches", ctypes.c_uint64)]
 
 
-KERNEL_FAMILIES = ["propagate", "update", "qr", "gemm", "qr_aux", "measure", "misc"]
+KERNEL_FAMILIES = ["propagate", "update", "qr", "gemm", "qr_aux", "measure", "misc", "lu"]
 
 
 class afqmc_timing(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_uint64 * 7), ("ms", ctypes.c_double * 7)]
+    _fields_ = [("launches", ctypes.c_uint64 * len(KERNEL_FAMILIES)), ("ms", ctypes.c_double * len(KERNEL_FAMILIES))]
 
 
 class afqmc_obs(ctypes.Structure):
@@ -185,8 +185,22 @@ def afqmc_det_ratio(h, slice_, site):
     return out[0], out[1]
 
 
-def afqmc_set_timing(h, enable):
-    _check(_lib.afqmc_set_timing(h, 1 if enable else 0), h)
+TIMING_ALL = (1 << len(KERNEL_FAMILIES)) - 1
+
+
+def afqmc_set_timing(h, families):
+    """families: True (all), False/0 (off), an int bit mask, or an iterable of family names."""
+    if families is True:
+        mask = TIMING_ALL
+    elif families is False or families is None:
+        mask = 0
+    elif isinstance(families, int):
+        mask = families
+    else:
+        mask = 0
+        for f in families:
+            mask |= 1 << KERNEL_FAMILIES.index(f)
+    _check(_lib.afqmc_set_timing(h, mask), h)
 
 
 def afqmc_get_timing(h):

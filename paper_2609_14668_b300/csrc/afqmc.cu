@@ -70,6 +70,7 @@ struct afqmc_handle {
     double *vtmp = nullptr, *Dp = nullptr, *sgn = nullptr, *tau = nullptr, *DbR = nullptr, *DsR = nullptr,
            *DbL = nullptr, *DsL = nullptr;
     unsigned int* flags = nullptr;
+    int* piv = nullptr;            // LU pivots of the middle matrix of G
     unsigned int epoch = 0;
     double2* blocks = nullptr;     // 4 operators x Nc x 4
     double2 *tw1 = nullptr, *tw2 = nullptr;
@@ -88,7 +89,7 @@ struct afqmc_handle {
     bool qr_smem_cols = false;     // QR keeps each CTA's columns in shared memory
     // launch accounting and optional per-launch event timing
     uint64_t launches = 0;
-    bool timing = false;
+    int timing = 0;                // bit mask of the timed kernel families
     uint64_t cat_launches[AFQMC_K_COUNT] = {};
     double cat_ms[AFQMC_K_COUNT] = {};
     std::vector<cudaEvent_t> ev_free;
@@ -187,7 +188,7 @@ struct Scope {
     Scope(afqmc_handle* h_, int c) : h(h_), cat(c) {
         h->launches += 1;
         h->cat_launches[c] += 1;
-        if (h->timing) {
+        if (h->timing & (1 << c)) {
             if (h->pending.size() > 50000) flush_timing(h);
             a = take_event(h);
             CK(cudaEventRecord(a, h->stream));
@@ -245,6 +246,23 @@ void qr(afqmc_handle* h, double* At) {
     CK(cudaLaunchCooperativeKernel((void*)k_qr_cols, grid, 256, args, smem, h->stream));
 }
 
+// P A = L U of the column-major A (At) in place, pivots in h->piv.
+void lu(afqmc_handle* h, double* At) {
+    const int n = h->N;
+    h->epoch += 1;
+    if (h->epoch == 0) {
+        CK(cudaMemsetAsync(h->flags, 0, sizeof(unsigned int) * n, h->stream));
+        h->epoch = 1;
+    }
+    LUArgs q{At, h->piv, h->flags, h->epoch, n, h->st};
+    const int grid = std::min(h->sms, n);
+    int in_smem = h->qr_smem_cols ? 1 : 0;
+    const size_t smem = sizeof(double) * (size_t)n * (in_smem ? 1 + (n + grid - 1) / grid : 1);
+    void* args[] = {&q, &in_smem};
+    Scope sc(h, AFQMC_K_LU);
+    CK(cudaLaunchCooperativeKernel((void*)k_lu_cols, grid, 256, args, smem, h->stream));
+}
+
 int warp_grid(int ncols) { return (ncols * 32 + 255) / 256; }
 int cpb_grid(int ncols) { return (ncols + CPB - 1) / CPB; }
 size_t cpb_smem(int n) { return sizeof(double) * (size_t)(CPB + 2) * n; }
@@ -290,7 +308,8 @@ void udt_extend(afqmc_handle* h, const UDTe& in, const UDTe& out, int lo, int hi
     gemm(h, F, 0, Tp, 0, out.T, 1.0, 0.0, nullptr, 0, nullptr, 0, /*a_upper=*/1);
 }
 
-// G = (1 + R L)^-1 with R = U_R D_R T_R, L^T = U_L D_L T_L (Loh-Gubernatis split).
+// G = (1 + R L)^-1 with R = U_R D_R T_R, L^T = U_L D_L T_L (Loh-Gubernatis split);
+// the well-conditioned middle matrix is solved by LU with partial pivoting.
 void form_green(afqmc_handle* h, const UDTe& R, const UDTe& Lt, double* Gout) {
     const int n = h->N;
     { Scope sc(h, AFQMC_K_MISC); k_split_scales<<<(n + 255) / 256, 256, 0, h->stream>>>(R.D, h->DbR, h->DsR, n); }
@@ -299,14 +318,14 @@ void form_green(afqmc_handle* h, const UDTe& R, const UDTe& Lt, double* Gout) {
     double* Mt = h->Wk[0];   // M column-major = M^T row-major
     gemm(h, Lt.Ut, 0, R.Ut, 1, Mt, 1.0, 0.0, h->DbL, 1, h->DbR, 1);
     gemm(h, Lt.T, 0, R.T, 1, Mt, 1.0, 1.0, h->DsL, 0, h->DsR, 0);
-    qr(h, Mt);
+    lu(h, Mt);
     double* Yt = h->Wk[1];   // Y = Db_R^-1 U_R^T, column-major
     {
         dim3 b(32, 8), g((n + 31) / 32, (n + 31) / 32);
         Scope sc(h, AFQMC_K_QRAUX);
         k_transpose_scale<<<g, b, 0, h->stream>>>(R.Ut, Yt, n, n, h->DbR, 1, nullptr, 0);
     }
-    { Scope sc(h, AFQMC_K_QRAUX); k_apply_qt<<<cpb_grid(n), 256, cpb_smem(n), h->stream>>>(Mt, h->tau, Yt, n, n); }
+    { Scope sc(h, AFQMC_K_QRAUX); k_fwdsolve_perm<<<cpb_grid(n), 256, cpb_smem(n), h->stream>>>(Mt, h->piv, Yt, n, n); }
     double* Wt = h->Wk[2];
     { Scope sc(h, AFQMC_K_QRAUX); k_backsolve<<<cpb_grid(n), 256, cpb_smem(n), h->stream>>>(Mt, Yt, Wt, n, n, h->DbL, h->st); }
     CK(cudaGetLastError());
@@ -578,7 +597,8 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         if (h->rowop_smem > 200 * 1024) throw CudaFail{AFQMC_E_INVALID, "lattice too large for the row kernel"};
         CK(raise_smem_limit((const void*)k_rowop, h->rowop_smem));
         if (N > PRE * 256) throw CudaFail{AFQMC_E_INVALID, "lattice too large for the column kernels"};
-        for (const void* f : {(const void*)k_apply_qt, (const void*)k_form_q, (const void*)k_backsolve})
+        for (const void* f : {(const void*)k_apply_qt, (const void*)k_form_q, (const void*)k_backsolve,
+                              (const void*)k_fwdsolve_perm})
             CK(raise_smem_limit(f, cpb_smem(N)));
         const size_t usmem = update_smem(h->W, h->nd, P.precision, N, h->sms);
         CK(raise_smem_limit((const void*)k_update_slice, usmem));
@@ -593,6 +613,9 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
             CK(raise_smem_limit((const void*)k_qr_cols, qsm));
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_qr_cols, 256, qsm));
             if (occ < 1) throw CudaFail{AFQMC_E_INVALID, "QR kernel does not fit on an SM"};
+            CK(raise_smem_limit((const void*)k_lu_cols, qsm));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lu_cols, 256, qsm));
+            if (occ < 1) throw CudaFail{AFQMC_E_INVALID, "LU kernel does not fit on an SM"};
         }
         // state
         h->field = h->dalloc<int8_t>((size_t)M * N);
@@ -614,6 +637,7 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         h->DbR = h->dalloc<double>(N); h->DsR = h->dalloc<double>(N);
         h->DbL = h->dalloc<double>(N); h->DsL = h->dalloc<double>(N);
         h->flags = h->dalloc<unsigned int>(N);
+        h->piv = h->dalloc<int>(N);
         CK(cudaMemset(h->flags, 0, sizeof(unsigned int) * N));
         h->st = h->dalloc<DevStatus>(1);
         CK(cudaMemset(h->st, 0, sizeof(DevStatus)));
@@ -832,10 +856,11 @@ afqmc_status afqmc_det_ratio(afqmc_handle* h, int32_t slice, int32_t site, doubl
     API_END(h)
 }
 
-afqmc_status afqmc_set_timing(afqmc_handle* h, int32_t enable) {
+afqmc_status afqmc_set_timing(afqmc_handle* h, int32_t family_mask) {
     API_BEGIN(h)
+    if (family_mask < 0 || family_mask > AFQMC_TIMING_ALL) { h->err = "timing mask outside the kernel families"; return AFQMC_E_INVALID; }
     flush_timing(h);
-    h->timing = enable != 0;
+    h->timing = family_mask;
     for (int c = 0; c < AFQMC_K_COUNT; ++c) { h->cat_launches[c] = 0; h->cat_ms[c] = 0.0; }
     return AFQMC_OK;
     API_END(h)

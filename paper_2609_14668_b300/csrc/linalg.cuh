@@ -276,6 +276,187 @@ __device__ __forceinline__ void store_vec(double* dst, int lo, int hi, const dou
     }
 }
 
+// ---------------------------------------------------------------------------
+// LU factorisation with partial pivoting of a column-major n x n matrix A
+// (array At), P A = L U: on exit L (unit lower, below the diagonal) and U
+// (upper, with the diagonal) overwrite At, piv[j] is the row swapped with row j
+// at step j.  Cooperative launch, the same column ownership, shared-memory
+// column storage and flag protocol as k_qr_cols; the critical path of a step
+// holds one reduction (the pivot search) instead of the two of a Householder
+// step.
+// ---------------------------------------------------------------------------
+struct LUArgs {
+    double* At; int* piv; unsigned int* flags; unsigned int epoch; int n;
+    DevStatus* st;
+};
+
+// pivot search, swap and scaling of column j (rows j..n-1), whole CTA
+__device__ void lu_pivot_column(const LUArgs& q, double* col, int j, double* redv, int* redi) {
+    const int n = q.n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    double best = -1.0;
+    int bi = j;
+    for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
+        const double v = fabs(col[i]);
+        if (v > best) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { redv[warp] = best; redi[warp] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nwarp; ++w)
+            if (redv[w] > best || (redv[w] == best && redi[w] < bi)) { best = redv[w]; bi = redi[w]; }
+        const double t = col[j];
+        col[j] = col[bi];
+        col[bi] = t;
+        redv[32] = col[j];
+        redi[32] = bi;
+        q.piv[j] = bi;
+        if (!(best > 0.0) || !isfinite(best)) flag_error(q.st, DERR_NUMERIC, 110);
+    }
+    __syncthreads();
+    const double inv = 1.0 / redv[32];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) col[i] *= inv;
+    __syncthreads();
+}
+
+__device__ void lu_publish(const LUArgs& q, const double* col, int j, bool copy) {
+    double* g = q.At + (size_t)j * q.n;
+    if (copy)
+        for (int i = threadIdx.x; i < q.n; i += blockDim.x) g[i] = col[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(&q.flags[j], q.epoch);
+    }
+}
+
+// apply step j (swap rows j, p; a_i -= l_ij a_j for i > j) to a column; one warp
+__device__ __forceinline__ void lu_apply_warp(const double* __restrict__ l, int p, double* col, int j, int n) {
+    const int lane = threadIdx.x & 31;
+    double aj = 0.0;
+    if (lane == 0) {
+        aj = col[p];
+        if (p != j) { col[p] = col[j]; col[j] = aj; }
+    }
+    aj = __shfl_sync(0xffffffffu, aj, 0);
+    __syncwarp();
+    for (int i = j + 1 + lane; i < n; i += 32) col[i] = fma(-l[i], aj, col[i]);
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(256) k_lu_cols(LUArgs q, int cols_in_smem) {
+    extern __shared__ double lu_smem[];
+    __shared__ double redv[33];
+    __shared__ int redi[33];
+    __shared__ int s_abort, s_piv;
+    const int n = q.n, G = gridDim.x, me = blockIdx.x;
+    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    double* l = lu_smem;                  // multipliers of the current step (rows j+1..n-1)
+    double* cols = lu_smem + n;
+    auto col = [&](int c) -> double* {
+        return cols_in_smem ? cols + (size_t)((c - me) / G) * n : q.At + (size_t)c * n;
+    };
+    if (threadIdx.x == 0) s_abort = 0;
+    if (cols_in_smem)
+        for (int c = me; c < n; c += G) {
+            double* d = col(c);
+            for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = q.At[(size_t)c * n + i];
+        }
+    __syncthreads();
+    if (me == 0) {
+        lu_pivot_column(q, col(0), 0, redv, redi);
+        lu_publish(q, col(0), 0, cols_in_smem);
+    }
+    for (int j = 0; j < n - 1; ++j) {
+        if (threadIdx.x == 0) {
+            volatile unsigned int* f = q.flags + j;
+            unsigned long long t0 = global_ns();
+            while (*f != q.epoch) {
+                if (*(volatile int*)&q.st->err) { s_abort = 1; break; }
+                if (global_ns() - t0 > WAIT_LIMIT_NS) { flag_error(q.st, DERR_TIMEOUT, 111); s_abort = 1; break; }
+            }
+            __threadfence();
+            s_piv = *(volatile int*)(q.piv + j);
+        }
+        __syncthreads();
+        if (s_abort) return;
+        const int p = s_piv;
+        const double* colj = q.At + (size_t)j * n;
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) l[i] = __ldcg(colj + i);
+        __syncthreads();
+        // lookahead: the owner of column j+1 finishes it first and publishes it
+        if ((j + 1) % G == me) {
+            double* c1 = col(j + 1);
+            if (threadIdx.x == 0) {
+                const double t = c1[p];
+                if (p != j) { c1[p] = c1[j]; c1[j] = t; }
+                redv[32] = t;
+            }
+            __syncthreads();
+            const double aj = redv[32];
+            for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) c1[i] = fma(-l[i], aj, c1[i]);
+            __syncthreads();
+            if (j + 1 < n - 1) lu_pivot_column(q, c1, j + 1, redv, redi);
+            else if (threadIdx.x == 0) q.piv[j + 1] = j + 1;
+            lu_publish(q, c1, j + 1, cols_in_smem);
+        }
+        int cnt = 0;
+        for (int c = j + 2 + ((me - (j + 2)) % G + G) % G; c < n; c += G, ++cnt)
+            if (cnt % nwarp == warp) lu_apply_warp(l, p, col(c), j, n);
+        __syncthreads();
+    }
+}
+
+// Y <- (L_{n-2} P_{n-2} ... L_0 P_0) Y for every column y (row of
+// Yt): at step j the swap of rows j and piv[j], then elimination with column j
+// of the unit lower triangle of the column-major Lt, as stored at step j.
+// 8 columns per CTA in shared memory, column j of L staged once per step and
+// prefetched one step ahead, the pivot list staged in shared memory.
+__global__ void __launch_bounds__(256) k_fwdsolve_perm(const double* __restrict__ Lt, const int* __restrict__ piv,
+                                                       double* Yt, int n, int ncols) {
+    extern __shared__ double cs_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = blockIdx.x * CPB;
+    double* lbuf = cs_smem;
+    double* y = cs_smem + n + (size_t)warp * n;
+    int* spiv = reinterpret_cast<int*>(cs_smem + (size_t)(CPB + 1) * n);
+    const int c = c0 + warp;
+    const bool has = c < ncols;
+    if (has)
+        for (int i = lane; i < n; i += 32) y[i] = Yt[(size_t)c * n + i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) spiv[i] = piv[i];
+    double pre[PRE];
+    prefetch_vec(Lt, 1, n, pre);
+    for (int j = 0; j < n - 1; ++j) {
+        __syncthreads();
+        store_vec(lbuf, j + 1, n, pre);
+        __syncthreads();
+        if (j + 1 < n - 1) prefetch_vec(Lt + (size_t)(j + 1) * n, j + 2, n, pre);
+        if (has) {
+            // step j of P A = L U: swap rows j and piv[j], then eliminate with column j of L
+            double yj = 0.0;
+            if (lane == 0) {
+                const int p = spiv[j];
+                yj = y[p];
+                if (p != j) { y[p] = y[j]; y[j] = yj; }
+            }
+            yj = __shfl_sync(0xffffffffu, yj, 0);
+            __syncwarp();
+            for (int i = j + 1 + lane; i < n; i += 32) y[i] = fma(-lbuf[i], yj, y[i]);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    if (has)
+        for (int i = lane; i < n; i += 32) Yt[(size_t)c * n + i] = y[i];
+}
+
 // Apply Q^T = H_{n-2} ... H_0 (H_0 first) to every column of Y (Yt rows).
 __global__ void __launch_bounds__(256) k_apply_qt(const double* __restrict__ Vt, const double* __restrict__ tau,
                                                   double* Yt, int n, int ncols) {

@@ -54,3 +54,19 @@ def test_beta_not_multiple_of_dtau():
     with pytest.raises(pkg.AfqmcError) as e:
         pkg.afqmc_create(p)
     assert e.value.code == 1
+
+
+def test_kernel_families_match_header():
+    """The binding's family names and timing struct follow the header's enum."""
+    import ctypes
+    import paper_2609_14668_b300 as pkg
+    src = open(os.path.join(ROOT, "include", "afqmc.h")).read()
+    fams = dict((k, int(v)) for k, v in re.findall(r"\bAFQMC_K_([A-Z]+)\s*=\s*(\d+)", src))
+    count = fams.pop("COUNT")
+    assert count == len(pkg.KERNEL_FAMILIES) == len(fams)
+    assert sorted(fams.values()) == list(range(count))
+    names = {"QRAUX": "qr_aux"}
+    for k, v in fams.items():
+        assert pkg.KERNEL_FAMILIES[v] == names.get(k, k.lower())
+    assert ctypes.sizeof(pkg.afqmc_timing) == 16 * count
+    assert pkg.TIMING_ALL == (1 << count) - 1

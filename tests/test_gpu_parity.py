@@ -190,3 +190,19 @@ def test_handles_of_different_sizes_coexist(pkg):
     assert st.accepted > 0
     small.close()
     big.close()
+
+
+def test_timing_mask_times_only_selected_families(pkg):
+    ch = make(pkg, 3, 1.0, 0.1, 3.73, 4, 5)
+    pkg.afqmc_set_timing(ch.h, ["update", "lu"])
+    ch.sweep(1)
+    t = pkg.afqmc_get_timing(ch.h)
+    assert t["update"][0] == 2 * ch.M and t["update"][1] > 0
+    assert t["lu"][0] > 0 and t["lu"][1] > 0
+    for fam in ("propagate", "gemm", "qr"):
+        assert t[fam][0] > 0 and t[fam][1] == 0.0
+    with pytest.raises(pkg.AfqmcError) as e:
+        pkg.afqmc_set_timing(ch.h, pkg.TIMING_ALL + 1)
+    assert e.value.code == 1
+    pkg.afqmc_set_timing(ch.h, 0)
+    ch.close()
