@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD_KEY, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tau-sweeps", type=int, default=15,
+                    help="extra sweeps per chain (after the timed and e2e ones) for the autocorrelation time")
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
                     help="1: split-TF32 tensor-core flush (the L=24 precision workload); 0: plain FP64")
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 sweep")
@@ -335,6 +337,31 @@ def time_chain(pkg, torch, args, key, precision, rank, world, dev, dist, stream)
                 timing=timing, breakdown=breakdown, dominant=dominant, obs=obs, clocks=ck, barrier=barrier)
 
 
+# DRAM bytes per launch of a kernel family from one ncu capture, valid only while
+# the kernel's source file still has the hash it had when the counters were taken
+# (profiles/k_update_slice_L24.md: same N and n_delay as the L=24 workload).
+CAPTURED_TRAFFIC = {
+    ("update", 1, 1152): ("paper_2609_14668_b300/csrc/update.cuh",
+                          "74c241640aaf0c60251a2b908f9e83598b3f0cf39b4c542e4ef07591fceac6ed",
+                          10.722048e6 + 0.118016e6),
+}
+
+
+def captured_traffic(fam, precision, N):
+    import hashlib
+    ent = CAPTURED_TRAFFIC.get((fam, precision, N))
+    if ent is None:
+        return None
+    path, sha, nbytes = ent
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), path), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != sha:
+                return None
+    except OSError:
+        return None
+    return nbytes
+
+
 def roofline_of(res, N, precision):
     """Roofline of the dominant kernel family: its algorithmic work per launch over
     its average launch duration, timed with events in the timed region."""
@@ -343,10 +370,12 @@ def roofline_of(res, N, precision):
     nl, tms = timing[fam]
     acc_per_update = accepted / max(timing["update"][0], 1)
     if fam == "update" and precision == 1:
-        # flush on the tensor cores: 3 TF32 products of 2 N^2 flops per accepted flip
-        fl = 3 * 2.0 * N * N * acc_per_update
-        peak, bound, unit = TF32_PEAK_TFLOPS, "tensor", "TFLOP/s"
-        note = "TF32 dense = measured BF16 burst x nominal TF32/BF16 ratio (1.1/2.25)"
+        # flush on the tensor cores: 2 N^2 algorithmic flops per accepted flip, each
+        # product done as three TF32 products (split-TF32), so the peak is TF32 / 3
+        fl = 2.0 * N * N * acc_per_update
+        peak, bound, unit = TF32_PEAK_TFLOPS / 3.0, "tensor", "TFLOP/s"
+        note = ("split-TF32 peak = TF32 dense / 3; TF32 dense = measured BF16 burst x nominal "
+                "TF32/BF16 ratio (1.1/2.25)")
     else:
         fl = algorithmic_flops(fam, N, Nc, acc_per_update)
         peak, bound, unit = FP64_PEAK_TFLOPS, "alu", "TFLOP/s"
@@ -355,7 +384,7 @@ def roofline_of(res, N, precision):
         return None
     ach = fl / (tms / nl / 1e3) / 1e12
     return {"bound": bound, "kernel": fam, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-            "traffic": None, "peak_note": note, "flops_per_launch": fl, "avg_launch_ms": tms / nl,
+            "traffic": captured_traffic(fam, precision, N), "peak_note": note, "flops_per_launch": fl, "avg_launch_ms": tms / nl,
             "share_of_step": breakdown[fam][1] / sum(v[1] for v in breakdown.values()),
             "share_note": "share of device time in one breakdown sweep per chain with every launch timed"}
 
@@ -385,6 +414,7 @@ def run_ours(args):
     ch = head["chain"]
     barrier = head["barrier"]
 
+    series = [[] for _ in head["chains"]]   # per-sweep observables of each chain
     # e2e: the public call a user makes per step (one sweep) plus reading the step's
     # results back to host memory (observable averages and the field); state stays resident.
     e2e = None
@@ -398,6 +428,7 @@ def run_ours(args):
                 o = chn.observables()
                 f = chn.field()
                 nb[c] = 10 * 8 + o["Czz"].nbytes + o["nk"].nbytes + f.nbytes
+                series[c].append(o)
         barrier()
         t0 = time.perf_counter()
         head["run_all"](e2e_steps)
@@ -410,6 +441,30 @@ def run_ours(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_val = head["total_proposed"] / float(t.item())
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": nbytes}
+
+    # autocorrelation: per-sweep energy and m^2 of every chain (e2e sweeps + extra ones)
+    if args.tau_sweeps > 0:
+        def more(c):
+            chn = head["chains"][c]
+            for _ in range(args.tau_sweeps):
+                chn.sweep(1)
+                series[c].append(chn.observables())
+        head["run_all"](more)
+    autocorr = None
+    if min(len(x) for x in series) >= 4:
+        from paper_2609_14668_b300.autocorr import tau_int
+        taus = {}
+        for k in ("energy", "m2"):
+            t, wdw, n = tau_int([[o[k] for o in x] for x in series])
+            taus[k] = {"tau_int": t, "window": wdw}
+        tmax = max(v["tau_int"] for v in taus.values())
+        autocorr = {"tau_int_sweeps": taus, "sweeps_per_chain": min(len(x) for x in series),
+                    "chains": len(series), "value_per_2tau": head["value"] / (2.0 * tmax),
+                    "definition": "tau_int = 1/2 + sum rho(t) over Sokal's window (c = 6), per-sweep averages, "
+                                  "chains pooled; corrected rate = value / (2 max tau_int)",
+                    "note": (f"chains start from a random field {args.warmup + 1 + args.steps} sweeps "
+                             "before the series; at L=24 that is short of equilibrium, so the relaxation "
+                             "inflates tau_int")}
 
     out = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps, "higher_is_better": True,
@@ -436,6 +491,8 @@ def run_ours(args):
                        "roofline": roofline_of(ref64, N, 0)}
     if e2e:
         out["e2e"] = e2e
+    if autocorr:
+        out["autocorr"] = autocorr
     if head["clocks"]:
         out["clocks"] = head["clocks"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
