@@ -1,5 +1,6 @@
 """Finite-temperature AFQMC (DQMC) for the half-filled honeycomb Hubbard model,
-spin-channel Ising field (HS-s^z), periodic boundaries: the real FP64 path.
+spin-channel Ising field (HS-s^z): periodic boundaries (the real FP64 path) or
+twisted boundaries (Sec. III.C: Peierls phases on the bonds, complex G).
 
 Follows Sec. II.B (Eqs. SzHS, coupling, ConfgWeight, GrFMat and the
 implementation notes 'First'..'Fifth') and Sec. III.B (Eqs. DetailBalance,
@@ -10,10 +11,11 @@ the momentum-space propagation of Sec. III.A that the CUDA path uses.
 
 Readings of the paper fixed here (the paper is silent or ambiguous):
   * the simulated spin is up; after the partial particle-hole transform the
-    down-spin propagator equals the up-spin one and contributes the scalar
-    e^{-gamma sum s}, so W(X) ~ e^{-gamma sum s} det(1 + B_M...B_1)^2 and a
-    single flip at (l, i) has weight ratio R = e^{2 gamma s_i} r^2 with
-    r = 1 + Delta (1 - G_ii), Delta = e^{-2 gamma s_i} - 1;
+    down-spin propagator is the complex conjugate of the up-spin one (equal to
+    it without a twist) and contributes the scalar e^{-gamma sum s}, so
+    W(X) ~ e^{-gamma sum s} |det(1 + B_M...B_1)|^2 and a single flip at (l, i)
+    has weight ratio R = e^{2 gamma s_i} |r|^2 with r = 1 + Delta (1 - G_ii),
+    Delta = e^{-2 gamma s_i} - 1 (real: the twist only enters the hopping);
   * a sweep is a forward pass l = 1..M (wrap into slice l, then propose every
     site i = 0..N-1 in ascending order) followed by a backward pass l = M..1
     (propose, then unwrap); accept iff u < R;
@@ -34,14 +36,15 @@ from . import rng as _rng
 class Model:
     """Static data: lattice, K, E = e^{-dtau K}, its inverse and half steps, gamma."""
 
-    def __init__(self, L, t=1.0, U=3.73, beta=3.0, dtau=0.1):
-        self.lat = Honeycomb(L, t=t)
+    def __init__(self, L, t=1.0, U=3.73, beta=3.0, dtau=0.1, theta=(0.0, 0.0)):
+        self.lat = Honeycomb(L, t=t, theta=theta)
         self.N = self.lat.N
         self.M = int(round(beta / dtau))
         if abs(self.M * dtau - beta) > 1e-9:
             raise ValueError("beta must be a multiple of dtau")
         self.t, self.U, self.beta, self.dtau = t, U, beta, dtau
         self.K = self.lat.hopping_matrix()
+        self.is_complex = np.iscomplexobj(self.K)
         # Eq. coupling: gamma_s = arccosh(e^{dtau U / 2})
         self.gamma = np.arccosh(np.exp(dtau * U / 2.0))
         self.E = expm_taylor(-dtau * self.K)
@@ -81,9 +84,12 @@ class Model:
     def log_weight(self, field):
         """log W(X) up to a field-independent constant: -gamma sum s + 2 log|det(1 + B_M..B_1)|.
 
-        The determinant is positive for the real path (it is a product of a
-        determinant with its complex conjugate, Sec. II.B 'Fourth')."""
+        W is the up-spin determinant times its complex conjugate (Sec. II.B
+        'Fourth'), so it is never negative; the returned sign is that of the
+        real determinant (real path) or 1 (twisted path)."""
         sign, ld = np.linalg.slogdet(np.eye(self.N) + self.chain_product(field, 1, self.M))
+        if self.is_complex:
+            sign = 1.0 if abs(sign) > 0 else 0.0
         return -self.gamma * float(field.sum()) + 2.0 * ld, sign
 
     # ---- stabilised chains -----------------------------------------------
@@ -114,10 +120,10 @@ class Model:
 def local_ratio(model, G, i, s_i):
     """Eq. rRatioLocal with the spin-channel Delta and the particle-hole weight factor.
 
-    Returns (R, r, Delta): R = W(X')/W(X) = e^{2 gamma s_i} r^2."""
+    Returns (R, r, Delta): R = W(X')/W(X) = e^{2 gamma s_i} |r|^2."""
     Delta = np.exp(-2.0 * model.gamma * s_i) - 1.0
     r = 1.0 + Delta * (1.0 - G[i, i])
-    return np.exp(2.0 * model.gamma * s_i) * r * r, r, Delta
+    return np.exp(2.0 * model.gamma * s_i) * (r * np.conj(r)).real, r, Delta
 
 
 class Chain:
@@ -166,7 +172,7 @@ class Chain:
             # Eq. DelayRatio: r = 1 + Delta {1 - G0_ii + sum_m x_m(i) y_m(i)}
             corr = sum(X[q][i] * Y[q][i] for q in range(len(X)))
             r = 1.0 + Delta * (1.0 - G0[i, i] + corr)
-            R = np.exp(2.0 * m.gamma * sig) * r * r
+            R = np.exp(2.0 * m.gamma * sig) * (r * np.conj(r)).real
             u = _rng.uniform(self.key, _rng.proposal_counter(self.sweep_index, pas, l, i, m.M, N))
             self.proposed += 1
             if u < R:                               # Eq. DetailBalance

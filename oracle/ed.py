@@ -107,11 +107,13 @@ def trotter_averages(lat, K, U, dtau, M):
                 acc_c[key] += (czz[key] * diag).sum()
             KX = np.tensordot(Ku, X, axes=(1, 0)) + np.matmul(Kd, X)
             acc_kin += KX[ia, ib, np.arange(du * dd)].sum()
+    # with a twist the sector matrices are complex; the traces are real up to rounding
+    Z, acc_d, acc_kin = np.real(Z), np.real(acc_d), np.real(acc_kin)
     D = acc_d / Z / N
     ekin = acc_kin / Z
     Czz = np.zeros((lat.L2, lat.L1))
     for (d1, d2), v in acc_c.items():
-        Czz[d2, d1] = v / Z / (2.0 * lat.Nc)
+        Czz[d2, d1] = np.real(v) / Z / (2.0 * lat.Nc)
     return dict(double_occ=D, energy=(ekin + N * U * D) / N, ekin=ekin / N, Czz=Czz)
 
 
@@ -129,8 +131,8 @@ def thermal_averages(lat, K, U, beta):
             w, V = np.linalg.eigh(H)
             p = np.exp(-beta * w)
             Z += p.sum()
-            acc_d += np.einsum("n,in,i,in->", p, V, docc.reshape(-1), V)
-            acc_kin += np.einsum("n,in,ij,jn->", p, V, H0, V)
+            acc_d += np.einsum("n,in,i,in->", p, V.conj(), docc.reshape(-1), V).real
+            acc_kin += np.einsum("n,in,ij,jn->", p, V.conj(), H0, V).real
     D = acc_d / Z / N
     ekin = acc_kin / Z
     return dict(double_occ=D, energy=(ekin + N * U * D) / N, ekin=ekin / N)

@@ -1,6 +1,6 @@
 """Exhaustive Hubbard-Stratonovich sum for tiny systems:
 <O> = sum_X W(X) O(X) / sum_X W(X)  (Eq. GSObsQMC) with the oracle's weight
-W(X) ~ e^{-gamma sum s} det(1 + B_M...B_1)^2 and the oracle's Wick measurement
+W(X) ~ e^{-gamma sum s} |det(1 + B_M...B_1)|^2 and the oracle's Wick measurement
 on G at slice 0."""
 import itertools
 import numpy as np
@@ -14,8 +14,8 @@ def hs_average(model, keys=("double_occ", "energy", "ekin", "Czz")):
     for bits in itertools.product((1, -1), repeat=N * M):
         field = np.array(bits, dtype=np.int8).reshape(M, N)
         lw, sign = model.log_weight(field)
-        if sign <= 0:
-            raise AssertionError("non-positive determinant on the real path")
+        if not sign > 0:
+            raise AssertionError("non-positive weight")
         logw.append(lw)
         o = measure(model, model.green_direct(field, M))
         obs.append({k: np.asarray(o[k], dtype=float) for k in keys})

@@ -79,6 +79,15 @@ class Honeycomb:
                 ks.append((l1 + self.theta[0]) / self.L1 * B1 + (l2 + self.theta[1]) / self.L2 * B2)
         return np.array(ks)
 
+    def qvectors(self):
+        """The untwisted grid q = (l1/L1) b1 + (l2/L2) b2 of the DFT over cells.
+
+        In Gauge-I the twist sits on the bonds, so K stays translation invariant:
+        the cell DFT with these q block-diagonalises it, and block q carries the
+        Bloch matrix at the shifted momentum k = q + A (kvectors)."""
+        return np.array([(l1 / self.L1) * B1 + (l2 / self.L2) * B2
+                         for l2 in range(self.L2) for l1 in range(self.L1)])
+
     def f_of_k(self, k):
         """f(k) = -t [1 + e^{i k.(a1-a2)} + e^{-i k.a2}] (below Eq. h0kMat)."""
         return -self.t * (1.0 + np.exp(1j * (k @ (A1 - A2))) + np.exp(-1j * (k @ A2)))

@@ -36,13 +36,16 @@ def expm_taylor(A, tol=1e-17, max_terms=60):
 
 
 def udt(A):
-    """A = U @ diag(D) @ T via QR with column pivoting; D is made positive."""
+    """A = U @ diag(D) @ T via QR with column pivoting; D is made positive by
+    moving the sign (real) or phase (complex) of R's diagonal into U."""
     Q, R, piv = sla.qr(A, pivoting=True, mode="full")
     d = np.diag(R).copy()
-    sgn = np.where(d < 0, -1.0, 1.0)
-    Q = Q * sgn[None, :]
-    R = R * sgn[:, None]
     D = np.abs(d)
+    ph = np.where(D > 0, d / np.where(D > 0, D, 1.0), 1.0)
+    if not np.iscomplexobj(A):
+        ph = np.where(d < 0, -1.0, 1.0)
+    Q = Q * ph[None, :]
+    R = R * np.conj(ph)[:, None]
     Tp = R / D[:, None]                    # upper triangular, unit diagonal, columns in pivot order
     T = np.empty_like(Tp)
     T[:, piv] = Tp                         # undo the column permutation: T = D^-1 R P^T
@@ -61,16 +64,19 @@ def udt_left_multiply(C, udt_in):
 
 
 def stable_green(udt_R, udt_L):
-    """G = (1 + R L)^-1 with R = U_R D_R T_R and L = (U_L D_L T_L)^T.
+    """G = (1 + R L)^-1 with R = U_R D_R T_R and L = (U_L D_L T_L)^T (plain
+    transpose), U_R and U_L unitary:
 
-    1 + R L = U_R Db_R [ Db_R^-1 U_R^T U_L Db_L^-1 + Ds_R T_R T_L^T Ds_L ] Db_L U_L^T,
-    Db = max(D, 1), Ds = min(D, 1).
+    1 + R L = U_R Db_R [ Db_R^-1 U_R^H conj(U_L) Db_L^-1 + Ds_R T_R T_L^T Ds_L ] Db_L U_L^T,
+    Db = max(D, 1), Ds = min(D, 1); for real matrices U^H = U^T and conj(U) = U.
     """
     UR, DR, TR = udt_R
     UL, DL, TL = udt_L
     DbR, DsR = np.maximum(DR, 1.0), np.minimum(DR, 1.0)
     DbL, DsL = np.maximum(DL, 1.0), np.minimum(DL, 1.0)
-    Mmid = (UR.T @ UL) / DbR[:, None] / DbL[None, :] + (DsR[:, None] * (TR @ TL.T)) * DsL[None, :]
-    rhs = UR.T / DbR[:, None]
+    URh = UR.conj().T
+    ULc = UL.conj()
+    Mmid = (URh @ ULc) / DbR[:, None] / DbL[None, :] + (DsR[:, None] * (TR @ TL.T)) * DsL[None, :]
+    rhs = URh / DbR[:, None]
     X = np.linalg.solve(Mmid, rhs)
-    return (UL / DbL[None, :]) @ X
+    return (ULc / DbL[None, :]) @ X

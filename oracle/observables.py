@@ -8,7 +8,10 @@ the asymmetric Trotter product.  Readings:
   * spin down follows from the partial particle-hole transform with the
     staggered sign kept:  G_dn_ij = (-1)^{i+j} (delta_ij - conj(G_up_ji));
   * Wick:  <n_ia n_jb> = n_ia n_jb + delta_ab (delta_ij - G^a_ji) G^a_ij,
-    n_ia = 1 - G^a_ii,  <c_i^+ c_j> = delta_ij - G_ji.
+    n_ia = 1 - G^a_ii,  <c_i^+ c_j> = delta_ij - G_ji;
+  * with a twist G is complex for one field: every Wick product is formed in
+    complex arithmetic and its real part taken at the end (the weight is real
+    and positive, and the imaginary parts average to zero).
 """
 import numpy as np
 
@@ -24,10 +27,10 @@ def measure(model, G):
     Gu = model.Eh @ G @ model.Ehinv
     Gd = spin_down_green(lat, Gu)
     I = np.eye(N)
-    nu = 1.0 - np.diag(Gu).real
-    nd = 1.0 - np.diag(Gd).real
+    nu = 1.0 - np.diag(Gu)
+    nd = 1.0 - np.diag(Gd)
     # double occupancy D = N_s^-1 sum_i <n_i_up n_i_dn> (Sec. II.C, after Eq. ChiCharge)
-    D = float(np.mean(nu * nd))
+    D = float(np.mean(nu * nd).real)
     # <H0> = sum_sigma sum_ij K_ij <c_i^+ c_j>  (App. C: E = <H0> + N_s U D)
     ekin = 0.0
     for Gs in (Gu, Gd):
@@ -60,12 +63,13 @@ def measure(model, G):
         return acc.real
     S0 = Szz(0, 0)
     Sdk = Szz(1, 0)                         # Gamma + b1/L (Eq. CrfRatio)
-    # n_ab(k) = N_c^-1 sum_{I,J} e^{i k.(r_I - r_J)} <a_I^+ b_J>  (Eq. nkMatrix, spin up)
+    # n_ab(k) = N_c^-1 sum_{I,J} e^{i q.(r_I - r_J)} <a_I^+ b_J>  (Eq. nkMatrix, spin up),
+    # q the cell-DFT grid; with a twist (Gauge-I) this is the occupation at k = q + A
     cd = I - Gu.T                           # cd[i, j] = <c_i^+ c_j>
     nk = np.zeros((L2, L1, 2, 2), dtype=complex)
     for l2 in range(L2):
         for l1 in range(L1):
-            k = lat.kvectors()[l1 + L1 * l2]
+            k = lat.qvectors()[l1 + L1 * l2]
             ph = np.array([np.exp(1j * (k @ lat.bravais_vector(*lat.cell_coords(c)))) for c in range(Nc)])
             for a in (0, 1):
                 for b in (0, 1):
@@ -73,4 +77,4 @@ def measure(model, G):
                     nk[l2, l1, a, b] = ph @ blk @ ph.conj() / Nc
     return dict(energy=energy, double_occ=D, ekin=ekin / N, Czz=Czz, S_af=S0, S_af_dk=Sdk,
                 m2=S0 / (2.0 * Nc), R_m2=1.0 - Sdk / S0, Czz_half=Czz[0, L1 // 2], nk=nk,
-                density=float(np.mean(nu + nd)))
+                density=float(np.mean(nu + nd).real))

@@ -95,17 +95,17 @@ def test_udt_reconstructs():
 
 # ---------------------------------------------------------------- closed forms
 def fermi_green_U0(lat, beta):
-    """G = (1 + e^{-beta K})^-1 from k space: G_k = 1/2 + tanh(beta|f|/2)/(2|f|) h(k), Fourier sum to r space."""
+    """G = (1 + e^{-beta K})^-1 from k space: G_k = 1/2 + tanh(beta|f|/2)/(2|f|) h(k) at the
+    (shifted) momentum k = q + A, Fourier sum to r space over the cell grid q (Gauge-I)."""
     Nc = lat.Nc
-    ks = lat.kvectors()
     r = np.array([lat.bravais_vector(*lat.cell_coords(c)) for c in range(Nc)])
     G = np.zeros((lat.N, lat.N), dtype=complex)
-    for k in ks:
+    for k, q in zip(lat.kvectors(), lat.qvectors()):
         f = lat.f_of_k(k)
         af = abs(f)
         c = 0.5 * beta if af < 1e-14 else np.tanh(0.5 * beta * af) / (2.0 * af)
         Gk = np.array([[0.5, c * f], [c * np.conj(f), 0.5]])
-        ph = np.exp(1j * r @ k)
+        ph = np.exp(1j * r @ q)
         P = np.outer(ph, ph.conj()) / Nc                # e^{i k (r_I - r_J)} / Nc
         for a in (0, 1):
             for b in (0, 1):
@@ -252,3 +252,129 @@ def test_trotter_ed_converges_to_thermal_ed():
     ex = ed.thermal_averages(lat, K, 4.0, 2.0)
     errs = [abs(ed.trotter_averages(lat, K, 4.0, 2.0 / M, M)["double_occ"] - ex["double_occ"]) for M in (16, 32, 64)]
     assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5
+
+
+# ---------------------------------------------------------------- twisted boundaries (complex G)
+TW = (0.25, 0.5)
+
+
+def test_block_form_of_twisted_propagator():
+    """With a twist the same (untwisted) DFT block-diagonalises E; the blocks are
+    e^{-dtau h(k)} at the shifted momenta k = ((l + theta)/L) b (Eqs. GaugeIPhase, kpoints)."""
+    L, dtau = 4, 0.1
+    lat = Honeycomb(L, theta=(0.3, 0.7))
+    E = expm_taylor(-dtau * lat.hopping_matrix())
+    q0 = Honeycomb(L).kvectors()
+    r = np.array([lat.bravais_vector(*lat.cell_coords(c)) for c in range(lat.Nc)])
+    UA = np.exp(-1j * q0 @ r.T) / L
+    Ufull = sla.block_diag(UA, UA)
+    Lam = Ufull @ E @ Ufull.conj().T
+    for q, k in enumerate(lat.kvectors()):
+        f = lat.f_of_k(k)
+        h = np.array([[0, f], [np.conj(f), 0]])
+        assert np.allclose(Lam[np.ix_([q, lat.Nc + q], [q, lat.Nc + q])], sla.expm(-dtau * h), atol=1e-13)
+    mask = np.ones_like(Lam, dtype=bool)
+    for q in range(lat.Nc):
+        mask[np.ix_([q, lat.Nc + q], [q, lat.Nc + q])] = False
+    assert np.abs(Lam[mask]).max() < 1e-13
+
+
+def test_expm_taylor_complex_hermitian():
+    K = Honeycomb(3, theta=TW).hopping_matrix()
+    assert np.iscomplexobj(K) and np.allclose(K, K.conj().T)
+    w, V = np.linalg.eigh(K)
+    for c in (-0.1, 0.05, -2.5):
+        ref = (V * np.exp(c * w)) @ V.conj().T
+        assert np.linalg.norm(expm_taylor(c * K) - ref, 2) <= 1e-14 * np.linalg.norm(ref, 2)
+
+
+def test_udt_reconstructs_complex():
+    rng_ = np.random.default_rng(2)
+    A = (rng_.standard_normal((12, 12)) + 1j * rng_.standard_normal((12, 12))) * np.logspace(0, 12, 12)[None, :]
+    U, D, T = udt(A)
+    assert np.allclose(U.conj().T @ U, np.eye(12), atol=1e-14)
+    assert np.all(D > 0)
+    assert np.allclose((U * D) @ T, A, rtol=1e-12, atol=1e-12 * np.abs(A).max())
+
+
+@pytest.mark.parametrize("L,beta,ns,theta", [(2, 2.0, 5, (0.3, 0.1)), (3, 3.0, 10, TW), (6, 6.0, 10, (0.75, 0.25))])
+def test_U0_green_closed_form_twisted(L, beta, ns, theta):
+    m = Model(L, U=0.0, beta=beta, dtau=0.1, theta=theta)
+    Gc = fermi_green_U0(m.lat, beta)
+    assert np.abs(Gc.imag).max() > 1e-3          # genuinely complex
+    field = random_field(m.M, m.N, 3)
+    for l in (0, m.M // 2, m.M):
+        assert np.abs(m.green_stable(field, l, ns) - Gc).max() < 1e-12
+
+
+def test_U0_observables_closed_form_twisted():
+    L, beta = 3, 3.0
+    m = Model(L, U=0.0, beta=beta, dtau=0.1, theta=TW)
+    o = measure(m, m.green_stable(random_field(m.M, m.N, 1), 0, 10))
+    fk = np.abs([m.lat.f_of_k(k) for k in m.lat.kvectors()])
+    assert abs(o["double_occ"] - 0.25) < 1e-12
+    assert abs(o["energy"] + (2.0 / m.N) * np.sum(fk * np.tanh(0.5 * beta * fk))) < 1e-12
+    for q, k in enumerate(m.lat.kvectors()):
+        f = m.lat.f_of_k(k)
+        nF = np.linalg.inv(np.eye(2) + sla.expm(beta * np.array([[0, f], [np.conj(f), 0]])))
+        assert np.allclose(o["nk"][q // L, q % L], nF.T, atol=1e-12)
+
+
+def test_stable_green_equals_plain_inverse_twisted():
+    m = Model(3, U=3.73, beta=2.0, dtau=0.1, theta=TW)
+    field = random_field(m.M, m.N, 7)
+    for l in (0, 3, 10, 20):
+        for ns in (1, 4, 10):
+            assert np.abs(m.green_stable(field, l, ns) - m.green_direct(field, l)).max() < 1e-11
+
+
+def test_ratio_equals_weight_ratio_twisted():
+    """R = e^{2 gamma s} |r|^2 equals W(X')/W(X) = e^{...} |det'|^2/|det|^2, and r the
+    ratio of the complex up-spin determinants."""
+    m = Model(2, U=3.73, beta=1.0, dtau=0.1, theta=TW)
+    field = random_field(m.M, m.N, 11)
+    lw0, _ = m.log_weight(field)
+    for l, i in ((1, 0), (4, 5), (10, 7)):
+        G = m.green_direct(field, l)
+        R, r, _ = local_ratio(m, G, i, float(field[l - 1, i]))
+        assert abs(np.imag(r)) > 1e-6
+        f2 = field.copy()
+        f2[l - 1, i] *= -1
+        lw1, _ = m.log_weight(f2)
+        assert abs(R - np.exp(lw1 - lw0)) < 1e-10 * max(1.0, R)
+        d0 = np.linalg.det(np.eye(m.N) + m.chain_product(field, 1, m.M))
+        d1 = np.linalg.det(np.eye(m.N) + m.chain_product(f2, 1, m.M))
+        assert abs(r - d1 / d0) < 1e-10 * max(1.0, abs(r))
+
+
+@pytest.mark.parametrize("n_delay", [1, 4])
+def test_slice_update_matches_fresh_green_twisted(n_delay):
+    m = Model(3, U=3.73, beta=1.0, dtau=0.1, theta=TW)
+    ch = Chain(m, n_delay=n_delay, n_stab=5, seed=9, field=random_field(m.M, m.N, 5))
+    ch.G = m.wrap(ch.G, ch.field[0])
+    ch.update_slice(1, 0)
+    assert ch.accepted > 0
+    assert np.abs(ch.G - m.green_direct(ch.field, 1)).max() < 1e-11
+
+
+def test_sweep_green_is_fresh_green_twisted():
+    m = Model(2, U=3.73, beta=1.0, dtau=0.1, theta=TW)
+    a = Chain(m, n_delay=1, n_stab=5, seed=4, field=random_field(m.M, m.N, 21))
+    b = Chain(m, n_delay=4, n_stab=5, seed=4, field=random_field(m.M, m.N, 21))
+    a.sweep()
+    b.sweep()
+    assert np.array_equal(a.field, b.field) and a.accepted == b.accepted > 0
+    assert np.abs(a.G - m.green_direct(a.field, 0)).max() < 1e-11
+    assert np.abs(a.G - b.G).max() < 1e-11
+
+
+@pytest.mark.slow
+def test_hs_sum_equals_trotter_ed_twisted():
+    """The same exact identity with complex hopping (twist): HS sum with weights
+    e^{-gamma sum s}|det|^2 and complex Wick contractions equals the Trotterised ED."""
+    m = Model(2, U=4.0, beta=0.4, dtau=0.2, theta=TW)
+    ref = ed.trotter_averages(m.lat, m.K, m.U, m.dtau, m.M)
+    got = hs_enum.hs_average(m)
+    for k in ("double_occ", "energy", "ekin"):
+        assert abs(got[k] - ref[k]) < 1e-10
+    assert np.abs(got["Czz"] - ref["Czz"]).max() < 1e-10
