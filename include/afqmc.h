@@ -30,9 +30,15 @@
  *     retrievable with afqmc_last_error(handle).  Numeric failures (NaN/Inf)
  *     and device-side wait timeouts return a status; nothing traps.
  *
- * Scope of this version: periodic boundaries (theta = 0), the spin-channel
- * field (hs_channel = 0), one Markov chain per handle; the real FP64 path,
- * optionally with a split-TF32 tensor-core flush (precision = 1).
+ * Scope of this version: the spin-channel field (hs_channel = 0), one Markov
+ * chain per handle, periodic (theta = 0: real G) or twisted (theta != 0:
+ * complex G, Sec. III.C) boundaries; FP64, optionally with a split-TF32
+ * tensor-core flush (precision = 1).
+ *
+ * Complex G (twisted boundaries): every N x N matrix that crosses this
+ * boundary (afqmc_get_G, afqmc_wrap_matrix, afqmc_update_slice) is complex,
+ * row-major, interleaved (re, im): 2 N^2 doubles.  On the device it is held as
+ * its real 2N x 2N embedding [[Re, -Im], [Im, Re]].
  */
 #ifndef AFQMC_H
 #define AFQMC_H
@@ -62,7 +68,8 @@ typedef struct {
     double t;              /* hopping amplitude */
     double U;              /* Hubbard repulsion (>= 0) */
     double beta, dtau;     /* M = beta/dtau must be an integer (|M dtau - beta| < 1e-9) */
-    double theta1, theta2; /* twist angles in units of 2 pi; must be 0 in this version */
+    double theta1, theta2; /* twist (Eq. kpoints: k = ((l + theta)/L) b), each in [0, 1);
+                              any nonzero value selects the complex path */
     int32_t hs_channel;    /* 0 = spin channel HS-s^z (Eq. SzHS); only 0 supported */
     int32_t n_delay;       /* delay rank n_d >= 1; 1 is the local Sherman-Morrison update */
     int32_t n_stab;        /* slices between QR recomputations of G; M % n_stab == 0 */
@@ -165,9 +172,10 @@ afqmc_status afqmc_update_slice(afqmc_handle* h, int32_t slice, int32_t pass,
                                 uint64_t sweep_index, double* G, int32_t* n_accepted);
 
 /* Weight ratio of flipping s[l-1][i] (Eqs. DRatio, rRatioLocal with the
- * particle-hole factor): out[0] = R = e^{2 gamma s} r^2, out[1] = r, using G at
- * slice l recomputed from scratch. */
-afqmc_status afqmc_det_ratio(afqmc_handle* h, int32_t slice, int32_t site, double out[2]);
+ * particle-hole factor): out[0] = R = e^{2 gamma s} |r|^2, out[1] = Re r,
+ * out[2] = Im r (0 with periodic boundaries), r = 1 + Delta (1 - G_ii), using G
+ * at slice l recomputed from scratch. */
+afqmc_status afqmc_det_ratio(afqmc_handle* h, int32_t slice, int32_t site, double out[3]);
 
 /* Per-launch CUDA-event timing of the kernel families whose bit (1 << AFQMC_K_*)
  * is set in family_mask; 0 disables timing, AFQMC_TIMING_ALL times every
@@ -216,7 +224,7 @@ afqmc_status afqmc_update_slice_noalloc(double* G_dev, int8_t* s_dev, int32_t N,
                                         int32_t n_delay, uint64_t seed, int32_t chain, void* cuda_stream,
                                         int32_t* n_accepted);
 
-/* Sizes of the handle: N, M, Nc. */
+/* Sizes of the handle: N (physical sites 2 Nc), M, Nc. */
 afqmc_status afqmc_dims(const afqmc_handle* h, int32_t* N, int32_t* M, int32_t* Nc);
 
 /* Message of the last failed call on h (never NULL).  With h == NULL: the last

@@ -104,14 +104,29 @@ def _dptr(a):
 
 
 # ----------------------------------------------------------------- C names
+# handles of twisted (complex-G) chains: their G buffers are complex128
+_COMPLEX = set()
+
+
+def _is_complex(h):
+    return ctypes.cast(h, ctypes.c_void_p).value in _COMPLEX
+
+
+def _gdtype(h):
+    return np.complex128 if _is_complex(h) else np.float64
+
+
 def afqmc_create(params, stream=None):
     h = _H()
     code = _lib.afqmc_create(ctypes.byref(params), ctypes.c_void_p(stream or 0), ctypes.byref(h))
     _check(code, None)
+    if params.theta1 != 0.0 or params.theta2 != 0.0:
+        _COMPLEX.add(ctypes.cast(h, ctypes.c_void_p).value)
     return h
 
 
 def afqmc_destroy(h):
+    _COMPLEX.discard(ctypes.cast(h, ctypes.c_void_p).value)
     _check(_lib.afqmc_destroy(h), h)
 
 
@@ -161,28 +176,29 @@ def afqmc_get_obs(h):
 
 def afqmc_get_G(h, slice_):
     N, _, _ = afqmc_dims(h)
-    G = np.empty((N, N))
+    G = np.empty((N, N), dtype=_gdtype(h))
     _check(_lib.afqmc_get_G(h, slice_, _dptr(G)), h)
     return G
 
 
 def afqmc_wrap_matrix(h, slice_, direction, A):
-    B = np.array(A, dtype=np.float64, order="C", copy=True)
+    B = np.array(A, dtype=_gdtype(h), order="C", copy=True)
     _check(_lib.afqmc_wrap_matrix(h, slice_, direction, _dptr(B)), h)
     return B
 
 
 def afqmc_update_slice(h, slice_, pas, sweep_index, G):
-    B = np.array(G, dtype=np.float64, order="C", copy=True)
+    B = np.array(G, dtype=_gdtype(h), order="C", copy=True)
     n = ctypes.c_int32()
     _check(_lib.afqmc_update_slice(h, slice_, pas, sweep_index, _dptr(B), ctypes.byref(n)), h)
     return B, n.value
 
 
 def afqmc_det_ratio(h, slice_, site):
-    out = np.empty(2)
+    """(R, r): r complex on the twisted path."""
+    out = np.empty(3)
     _check(_lib.afqmc_det_ratio(h, slice_, site, _dptr(out)), h)
-    return out[0], out[1]
+    return out[0], (complex(out[1], out[2]) if _is_complex(h) else out[1])
 
 
 TIMING_ALL = (1 << len(KERNEL_FAMILIES)) - 1
@@ -232,8 +248,9 @@ def afqmc_last_error(h=None):
 
 
 def make_params(L, beta, dtau, U, n_delay, n_stab, t=1.0, seed=0, chain=0, measure=0, device=0, L2=None,
-                precision=0):
-    return afqmc_params(L1=L, L2=L if L2 is None else L2, t=t, U=U, beta=beta, dtau=dtau, theta1=0.0, theta2=0.0,
+                precision=0, theta=(0.0, 0.0)):
+    return afqmc_params(L1=L, L2=L if L2 is None else L2, t=t, U=U, beta=beta, dtau=dtau,
+                        theta1=float(theta[0]), theta2=float(theta[1]),
                         hs_channel=0, n_delay=n_delay, n_stab=n_stab, precision=precision, measure=measure,
                         chain=chain, device=device, seed=seed)
 

@@ -51,7 +51,12 @@ enum Op { OP_E = 0, OP_EINV = 1, OP_EH = 2, OP_EHINV = 3 };
 
 struct afqmc_handle {
     afqmc_params p{};
-    int N = 0, Nc = 0, L1 = 0, L2 = 0, M = 0, ns = 0, nc = 0, nd = 0, W = UPD_WMAX;
+    // Np = 2 Nc physical sites; N = dimension of the device matrices: Np, or 2 Np
+    // for twisted boundaries, where every complex N x N matrix is held as its
+    // real embedding [[Re, -Im], [Im, Re]] (cplx = 1)
+    int N = 0, Np = 0, Nc = 0, L1 = 0, L2 = 0, M = 0, ns = 0, nc = 0, nd = 0, W = UPD_WMAX;
+    int cplx = 0;
+    BondPhases bond_ph{};          // e^{i Phi} of the three bonds (measurements)
     double gamma = 0.0, egp = 1.0, egm = 1.0;      // e^{gamma}, e^{-gamma}
     double dl_p = 0.0, dl_m = 0.0, ef_p = 1.0, ef_m = 1.0;
     uint64_t key = 0, sweep_index = 0;
@@ -118,10 +123,13 @@ int radices(int n, int* r) {
     return n == 1 ? k : -1;
 }
 
-// f(k) = -t [1 + e^{i k.(a1-a2)} + e^{-i k.a2}] (below Eq. h0kMat),
-// k = (l1/L1) b1 + (l2/L2) b2 so k.a_alpha = 2 pi l_alpha / L_alpha.
-std::complex<double> bloch_f(double t, int l1, int l2, int L1, int L2) {
-    const double p1 = 2.0 * M_PI * l1 / L1, p2 = 2.0 * M_PI * l2 / L2;
+// f(k) = -t [1 + e^{i k.(a1-a2)} + e^{-i k.a2}] (below Eq. h0kMat) at
+// k = ((l1 + theta1)/L1) b1 + ((l2 + theta2)/L2) b2 (Eq. kpoints), so
+// k.a_alpha = 2 pi (l_alpha + theta_alpha) / L_alpha.  In Gauge-I (Sec. III.C)
+// the twist sits on the bonds and K stays translation invariant: block l of
+// the untwisted cell DFT is the Bloch matrix at this shifted k.
+std::complex<double> bloch_f(double t, int l1, int l2, int L1, int L2, double th1, double th2) {
+    const double p1 = 2.0 * M_PI * (l1 + th1) / L1, p2 = 2.0 * M_PI * (l2 + th2) / L2;
     const std::complex<double> I(0.0, 1.0);
     return -t * (1.0 + std::exp(I * (p1 - p2)) + std::exp(-I * p2));
 }
@@ -205,18 +213,18 @@ struct Scope {
 };
 void launch_rowop(afqmc_handle* h, const double* in, double* out, int nrows, Op op, DiagScale pre, DiagScale post,
                   bool transpose) {
-    const int per = 2 * h->vp;
+    const int per = h->cplx ? h->vp : 2 * h->vp;
     const int grid = (nrows + per - 1) / per;
     Scope sc(h, AFQMC_K_PROPAGATE);
     k_rowop<<<grid, 256, h->rowop_smem, h->stream>>>(in, out, nrows, h->N, h->N, h->plan,
                                                      h->blocks + (size_t)op * h->Nc * 4, pre, post,
-                                                     transpose ? 1 : 0, h->vp);
+                                                     transpose ? 1 : 0, h->vp, h->cplx);
     CK(cudaGetLastError());
 }
 
 DiagScale no_scale() { return DiagScale{nullptr, 1.0, 1.0}; }
 DiagScale vscale(afqmc_handle* h, int l, int sign) {   // e^{sign gamma s_l}
-    const int8_t* s = h->field + (size_t)(l - 1) * h->N;
+    const int8_t* s = h->field + (size_t)(l - 1) * h->Np;
     return sign > 0 ? DiagScale{s, h->egp, h->egm} : DiagScale{s, h->egm, h->egp};
 }
 
@@ -365,11 +373,12 @@ void update_slice(afqmc_handle* h, double* G, int l, int pass, uint64_t sweep) {
     UpdArgs a{};
     a.G = G; a.N = h->N; a.Xs = h->Xs; a.Ys = h->Ys; a.msite = h->msite; a.mcoef = h->mcoef;
     a.xw = h->xw; a.yw = h->yw; a.Gw = h->Gw; a.ctl = h->ctl;
-    a.s = h->field + (size_t)(l - 1) * h->N;
+    a.s = h->field + (size_t)(l - 1) * h->Np;
     a.nd = h->nd; a.W = h->W;
+    a.pair = h->cplx; a.Np = h->Np;
     a.dl_p = h->dl_p; a.dl_m = h->dl_m; a.ef_p = h->ef_p; a.ef_m = h->ef_m;
     a.key = h->key;
-    a.ctr0 = ((sweep * 2 + (uint64_t)pass) * (uint64_t)h->M + (uint64_t)(l - 1)) * (uint64_t)h->N + 1;
+    a.ctr0 = ((sweep * 2 + (uint64_t)pass) * (uint64_t)h->M + (uint64_t)(l - 1)) * (uint64_t)h->Np + 1;
     a.n_acc = h->n_acc; a.st = h->st;
     a.precision = h->p.precision;
     const size_t smem = update_smem(h->W, h->nd, h->p.precision, h->N, h->sms);
@@ -381,16 +390,17 @@ void update_slice(afqmc_handle* h, double* G, int l, int pass, uint64_t sweep) {
 void measure(afqmc_handle* h, const double* G, bool accumulate) {
     double* g = h->Wk[5];
     half_step(h, G, g);
-    { Scope sc(h, AFQMC_K_MEASURE); k_measure_pairs<<<h->Nc, 128, 0, h->stream>>>(g, h->L1, h->L2, h->czz, h->hab); }
+    const GView gv{g, h->Np, h->N, h->cplx};
+    { Scope sc(h, AFQMC_K_MEASURE); k_measure_pairs<<<h->Nc, 128, 0, h->stream>>>(gv, h->L1, h->L2, h->czz, h->hab); }
     CK(cudaGetLastError());
     if (accumulate) {
         { Scope sc(h, AFQMC_K_MEASURE); k_measure_nk<<<(h->Nc + 127) / 128, 128, 0, h->stream>>>(h->hab, h->L1, h->L2, h->tw1, h->tw2, h->nk_acc, 1); }
-        { Scope sc(h, AFQMC_K_MEASURE); k_measure_scalars<<<1, 256, 0, h->stream>>>(g, h->czz, h->L1, h->L2, h->p.t, h->p.U, h->tw1, h->obs_acc,
-                                                    h->czz_acc, 1, h->obs_count, h->st); }
+        { Scope sc(h, AFQMC_K_MEASURE); k_measure_scalars<<<1, 256, 0, h->stream>>>(gv, h->czz, h->L1, h->L2, h->p.t, h->p.U, h->tw1,
+                                                    h->bond_ph, h->obs_acc, h->czz_acc, 1, h->obs_count, h->st); }
     } else {
         { Scope sc(h, AFQMC_K_MEASURE); k_measure_nk<<<(h->Nc + 127) / 128, 128, 0, h->stream>>>(h->hab, h->L1, h->L2, h->tw1, h->tw2, h->nk_now, 0); }
-        { Scope sc(h, AFQMC_K_MEASURE); k_measure_scalars<<<1, 256, 0, h->stream>>>(g, h->czz, h->L1, h->L2, h->p.t, h->p.U, h->tw1, h->obs_now,
-                                                    nullptr, 0, nullptr, h->st); }
+        { Scope sc(h, AFQMC_K_MEASURE); k_measure_scalars<<<1, 256, 0, h->stream>>>(gv, h->czz, h->L1, h->L2, h->p.t, h->p.U, h->tw1,
+                                                    h->bond_ph, h->obs_now, nullptr, 0, nullptr, h->st); }
         CK(cudaMemcpyAsync(h->czz_now, h->czz, sizeof(double) * h->Nc, cudaMemcpyDeviceToDevice, h->stream));
     }
     CK(cudaGetLastError());
@@ -477,6 +487,30 @@ void green_at(afqmc_handle* h, int l, double* out) {
     form_green(h, cur, a, out);
 }
 
+// Host <-> device matrix transfer of the API: real N x N, or (twisted) a complex
+// Np x Np host matrix (interleaved re, im) to and from the device embedding,
+// through the staging buffer `stage` (>= 2 Np^2 doubles).
+void from_host(afqmc_handle* h, const double* host, double* dev, double* stage) {
+    if (!h->cplx) {
+        CK(cudaMemcpyAsync(dev, host, sizeof(double) * h->N * h->N, cudaMemcpyHostToDevice, h->stream));
+        return;
+    }
+    const size_t n2 = (size_t)h->Np * h->Np;
+    CK(cudaMemcpyAsync(stage, host, sizeof(double2) * n2, cudaMemcpyHostToDevice, h->stream));
+    { Scope sc(h, AFQMC_K_MISC); k_embed<<<(unsigned)((n2 + 255) / 256), 256, 0, h->stream>>>((const double2*)stage, dev, h->Np); }
+    CK(cudaGetLastError());
+}
+void to_host(afqmc_handle* h, const double* dev, double* host, double* stage) {
+    if (!h->cplx) {
+        CK(cudaMemcpyAsync(host, dev, sizeof(double) * h->N * h->N, cudaMemcpyDeviceToHost, h->stream));
+        return;
+    }
+    const size_t n2 = (size_t)h->Np * h->Np;
+    { Scope sc(h, AFQMC_K_MISC); k_extract<<<(unsigned)((n2 + 255) / 256), 256, 0, h->stream>>>(dev, (double2*)stage, h->Np); }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(host, stage, sizeof(double2) * n2, cudaMemcpyDeviceToHost, h->stream));
+}
+
 // ------------------------------------------------------------------ allocation-free slice update
 // One file-scope scratch array for afqmc_update_slice_noalloc (callers that
 // cannot allocate device memory).  Layout, in bytes from the start:
@@ -541,7 +575,8 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
     if (P.L1 < 1 || P.L2 < 1 || P.L1 > 64 || P.L2 > 64) return bad("L1, L2 must be in [1, 64]");
     if (!(P.beta > 0) || !(P.dtau > 0)) return bad("beta and dtau must be positive");
     if (!(P.U >= 0)) return bad("U must be >= 0");
-    if (P.theta1 != 0.0 || P.theta2 != 0.0) return bad("twisted boundaries are not supported in this version");
+    if (!(P.theta1 >= 0.0 && P.theta1 < 1.0 && P.theta2 >= 0.0 && P.theta2 < 1.0))
+        return bad("twist angles theta1, theta2 must be in [0, 1)");
     if (P.hs_channel != 0) return bad("only the spin channel (hs_channel = 0) is supported");
     if (P.precision != 0 && P.precision != 1) return bad("precision must be 0 (FP64) or 1 (split-TF32 flush)");
     const double Mr = P.beta / P.dtau;
@@ -552,8 +587,19 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
     auto* h = new afqmc_handle();
     try {
         h->p = P;
-        h->L1 = P.L1; h->L2 = P.L2; h->Nc = P.L1 * P.L2; h->N = 2 * h->Nc; h->M = M;
-        h->ns = P.n_stab; h->nc = M / P.n_stab; h->nd = P.n_delay;
+        h->L1 = P.L1; h->L2 = P.L2; h->Nc = P.L1 * P.L2; h->Np = 2 * h->Nc; h->M = M;
+        h->cplx = (P.theta1 != 0.0 || P.theta2 != 0.0) ? 1 : 0;
+        h->N = h->cplx ? 2 * h->Np : h->Np;
+        h->ns = P.n_stab; h->nc = M / P.n_stab;
+        // a physical flip is two rank-1 moves of the embedding when twisted
+        h->nd = h->cplx ? 2 * P.n_delay : P.n_delay;
+        {
+            const int dd1[3] = {0, 1, 0}, dd2[3] = {0, -1, -1};   // bond displacements (Gauge-I)
+            for (int e = 0; e < 3; ++e) {
+                const double phi = 2.0 * M_PI * (P.theta1 * dd1[e] / P.L1 + P.theta2 * dd2[e] / P.L2);
+                h->bond_ph.e[e] = make_double2(std::cos(phi), std::sin(phi));
+            }
+        }
         h->W = std::min(UPD_WMAX, h->N);
         h->gamma = std::acosh(std::exp(P.dtau * P.U / 2.0));     // Eq. coupling
         h->egp = std::exp(h->gamma); h->egm = std::exp(-h->gamma);
@@ -564,11 +610,11 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         CK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, P.device));
         if (cuda_stream) h->stream = (cudaStream_t)cuda_stream;
         else { CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)); h->own_stream = true; }
-        const int N = h->N, Nc = h->Nc;
+        const int N = h->N, Np = h->Np, Nc = h->Nc;
         const size_t nn = (size_t)N * N;
         // FFT plan, twiddles, propagator blocks
         FFTPlan& pl = h->plan;
-        pl.N = N; pl.Nc = Nc; pl.L1 = h->L1; pl.L2 = h->L2;
+        pl.N = Np; pl.Nc = Nc; pl.L1 = h->L1; pl.L2 = h->L2;
         pl.nr1 = radices(h->L1, pl.r1);
         pl.nr2 = radices(h->L2, pl.r2);
         for (int q = 0; q < pl.nr1; ++q) if (pl.r1[q] > 8) pl.nr1 = -1;
@@ -588,12 +634,13 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
             for (int l2 = 0; l2 < h->L2; ++l2)
                 for (int l1 = 0; l1 < h->L1; ++l1) {
                     const int q = l1 + h->L1 * l2;
-                    block_exp(bloch_f(P.t, l1, l2, h->L1, h->L2), cs[op], &blk[((size_t)op * Nc + q) * 4]);
+                    block_exp(bloch_f(P.t, l1, l2, h->L1, h->L2, P.theta1, P.theta2), cs[op],
+                              &blk[((size_t)op * Nc + q) * 4]);
                 }
         h->blocks = h->dalloc<double2>(blk.size());
         CK(cudaMemcpy(h->blocks, blk.data(), sizeof(double2) * blk.size(), cudaMemcpyHostToDevice));
-        h->vp = std::max(1, std::min(4, (int)(48000 / (sizeof(double2) * 2 * (size_t)N))));
-        h->rowop_smem = sizeof(double2) * 2 * (size_t)h->vp * N;
+        h->vp = std::max(1, std::min(4, (int)(48000 / (sizeof(double2) * 2 * (size_t)Np))));
+        h->rowop_smem = sizeof(double2) * 2 * (size_t)h->vp * Np;
         if (h->rowop_smem > 200 * 1024) throw CudaFail{AFQMC_E_INVALID, "lattice too large for the row kernel"};
         CK(raise_smem_limit((const void*)k_rowop, h->rowop_smem));
         if (N > PRE * 256) throw CudaFail{AFQMC_E_INVALID, "lattice too large for the column kernels"};
@@ -618,7 +665,7 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
             if (occ < 1) throw CudaFail{AFQMC_E_INVALID, "LU kernel does not fit on an SM"};
         }
         // state
-        h->field = h->dalloc<int8_t>((size_t)M * N);
+        h->field = h->dalloc<int8_t>((size_t)M * Np);
         h->G = h->dalloc<double>(nn);
         for (auto& w : h->Wk) w = h->dalloc<double>(nn);
         h->Xs = h->dalloc<double>((size_t)h->nd * N);
@@ -644,7 +691,7 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         h->n_acc = h->dalloc<unsigned long long>(1);
         h->drift = h->dalloc<unsigned long long>(1);
         h->czz = h->dalloc<double>(Nc);
-        h->hab = h->dalloc<double>((size_t)4 * Nc);
+        h->hab = h->dalloc<double>((size_t)8 * Nc);
         h->obs_now = h->dalloc<double>(OBS_SCALARS);
         h->czz_now = h->dalloc<double>(Nc);
         h->nk_now = h->dalloc<double>((size_t)8 * Nc);
@@ -663,7 +710,7 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
             for (auto& e : *st) { e.Ut = h->dalloc<double>(nn); e.T = h->dalloc<double>(nn); e.D = h->dalloc<double>(N); }
         for (auto* e : {&h->tmpA, &h->tmpB}) { e->Ut = h->dalloc<double>(nn); e->T = h->dalloc<double>(nn); e->D = h->dalloc<double>(N); }
         // initial field from the counter-based stream, then stacks and G
-        { Scope sc(h, AFQMC_K_MISC); k_init_field<<<(unsigned)(((size_t)M * N + 255) / 256), 256, 0, h->stream>>>(h->field, M, N, h->key); }
+        { Scope sc(h, AFQMC_K_MISC); k_init_field<<<(unsigned)(((size_t)M * Np + 255) / 256), 256, 0, h->stream>>>(h->field, M, Np, h->key); }
         CK(cudaGetLastError());
         init_chain(h);
         afqmc_status s = check_device(h);
@@ -708,7 +755,7 @@ afqmc_status afqmc_destroy(afqmc_handle* h) {
 afqmc_status afqmc_set_field(afqmc_handle* h, const int8_t* s, uint64_t sweep_index) {
     API_BEGIN(h)
     if (!s) { h->err = "null field"; return AFQMC_E_INVALID; }
-    const size_t len = (size_t)h->M * h->N;
+    const size_t len = (size_t)h->M * h->Np;
     for (size_t o = 0; o < len; ++o)
         if (s[o] != 1 && s[o] != -1) { h->err = "field entries must be +1 or -1"; return AFQMC_E_INVALID; }
     CK(cudaMemcpyAsync(h->field, s, len, cudaMemcpyHostToDevice, h->stream));
@@ -721,7 +768,7 @@ afqmc_status afqmc_set_field(afqmc_handle* h, const int8_t* s, uint64_t sweep_in
 afqmc_status afqmc_get_field(afqmc_handle* h, int8_t* s) {
     API_BEGIN(h)
     if (!s) { h->err = "null field"; return AFQMC_E_INVALID; }
-    CK(cudaMemcpyAsync(s, h->field, (size_t)h->M * h->N, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(s, h->field, (size_t)h->M * h->Np, cudaMemcpyDeviceToHost, h->stream));
     return check_device(h);
     API_END(h)
 }
@@ -738,8 +785,8 @@ afqmc_status afqmc_sweep(afqmc_handle* h, int32_t n_sweeps, afqmc_sweep_stats* s
         CK(cudaMemcpyAsync(&acc, h->n_acc, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaMemcpyAsync(&dr, h->drift, sizeof(dr), cudaMemcpyDeviceToHost, h->stream));
         afqmc_status s = check_device(h);
-        stats->proposed = (uint64_t)n_sweeps * 2ull * (uint64_t)h->N * (uint64_t)h->M;
-        stats->accepted = acc;
+        stats->proposed = (uint64_t)n_sweeps * 2ull * (uint64_t)h->Np * (uint64_t)h->M;
+        stats->accepted = h->cplx ? acc / 2 : acc;       // two moves per flip when twisted
         double d;
         std::memcpy(&d, &dr, sizeof(d));
         stats->max_stab_drift = d;
@@ -800,7 +847,7 @@ afqmc_status afqmc_get_G(afqmc_handle* h, int32_t slice, double* out) {
     if (!out || slice < 0 || slice > h->M) { h->err = "bad slice or null output"; return AFQMC_E_INVALID; }
     double* dst = h->Wk[5];
     green_at(h, slice, dst);
-    CK(cudaMemcpyAsync(out, dst, sizeof(double) * h->N * h->N, cudaMemcpyDeviceToHost, h->stream));
+    to_host(h, dst, out, h->Wk[4]);
     return check_device(h);
     API_END(h)
 }
@@ -809,14 +856,13 @@ afqmc_status afqmc_wrap_matrix(afqmc_handle* h, int32_t slice, int32_t direction
     API_BEGIN(h)
     if (!A || slice < 1 || slice > h->M || direction < -1 || direction > 1) { h->err = "bad arguments"; return AFQMC_E_INVALID; }
     double* d = h->Wk[3];
-    const size_t bytes = sizeof(double) * h->N * h->N;
-    CK(cudaMemcpyAsync(d, A, bytes, cudaMemcpyHostToDevice, h->stream));
+    from_host(h, A, d, h->Wk[2]);
     if (direction == 0) {
         half_step(h, d, h->Wk[5]);
-        CK(cudaMemcpyAsync(A, h->Wk[5], bytes, cudaMemcpyDeviceToHost, h->stream));
+        to_host(h, h->Wk[5], A, h->Wk[2]);
     } else {
         wrap(h, d, slice, direction);
-        CK(cudaMemcpyAsync(A, d, bytes, cudaMemcpyDeviceToHost, h->stream));
+        to_host(h, d, A, h->Wk[2]);
     }
     return check_device(h);
     API_END(h)
@@ -827,31 +873,31 @@ afqmc_status afqmc_update_slice(afqmc_handle* h, int32_t slice, int32_t pass, ui
     API_BEGIN(h)
     if (!G || slice < 1 || slice > h->M || (pass != 0 && pass != 1)) { h->err = "bad arguments"; return AFQMC_E_INVALID; }
     double* d = h->Wk[5];
-    const size_t bytes = sizeof(double) * h->N * h->N;
-    CK(cudaMemcpyAsync(d, G, bytes, cudaMemcpyHostToDevice, h->stream));
+    from_host(h, G, d, h->Wk[4]);
     CK(cudaMemsetAsync(h->n_acc, 0, sizeof(unsigned long long), h->stream));
     update_slice(h, d, slice, pass, sweep_index);
     unsigned long long acc = 0;
-    CK(cudaMemcpyAsync(G, d, bytes, cudaMemcpyDeviceToHost, h->stream));
+    to_host(h, d, G, h->Wk[4]);
     CK(cudaMemcpyAsync(&acc, h->n_acc, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
     afqmc_status s = check_device(h);
-    if (n_accepted) *n_accepted = (int32_t)acc;
+    if (n_accepted) *n_accepted = (int32_t)(h->cplx ? acc / 2 : acc);
     return s;
     API_END(h)
 }
 
-afqmc_status afqmc_det_ratio(afqmc_handle* h, int32_t slice, int32_t site, double out[2]) {
+afqmc_status afqmc_det_ratio(afqmc_handle* h, int32_t slice, int32_t site, double out[3]) {
     API_BEGIN(h)
-    if (!out || slice < 1 || slice > h->M || site < 0 || site >= h->N) { h->err = "bad arguments"; return AFQMC_E_INVALID; }
+    if (!out || slice < 1 || slice > h->M || site < 0 || site >= h->Np) { h->err = "bad arguments"; return AFQMC_E_INVALID; }
     double* g = h->Wk[5];
     green_at(h, slice, g);
     int8_t sv = 0;
-    CK(cudaMemcpyAsync(&sv, h->field + (size_t)(slice - 1) * h->N + site, 1, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&sv, h->field + (size_t)(slice - 1) * h->Np + site, 1, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     double* o = h->vtmp;
-    { Scope sc(h, AFQMC_K_MISC); k_ratio<<<1, 1, 0, h->stream>>>(g, h->N, site, sv, h->dl_p, h->dl_m, h->ef_p, h->ef_m, o); }
+    const GView gv{g, h->Np, h->N, h->cplx};
+    { Scope sc(h, AFQMC_K_MISC); k_ratio<<<1, 1, 0, h->stream>>>(gv, site, sv, h->dl_p, h->dl_m, h->ef_p, h->ef_m, o); }
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(out, o, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(out, o, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     return check_device(h);
     API_END(h)
 }
@@ -910,7 +956,7 @@ afqmc_status afqmc_update_slice_noalloc(double* G_dev, int8_t* s_dev, int32_t N,
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     const double gamma = std::acosh(std::exp(dtau * U / 2.0));
     UpdArgs a{};
-    a.G = G_dev; a.N = N;
+    a.G = G_dev; a.N = N; a.Np = N; a.pair = 0;
     a.Xs = reinterpret_cast<double*>(base + NA_OFF_XS);
     a.Ys = reinterpret_cast<double*>(base + NA_OFF_YS);
     a.msite = reinterpret_cast<int*>(base + NA_OFF_SITE);
@@ -952,7 +998,7 @@ afqmc_status afqmc_update_slice_noalloc(double* G_dev, int8_t* s_dev, int32_t N,
 
 afqmc_status afqmc_dims(const afqmc_handle* h, int32_t* N, int32_t* M, int32_t* Nc) {
     if (!h) return AFQMC_E_INVALID;
-    if (N) *N = h->N;
+    if (N) *N = h->Np;
     if (M) *M = h->M;
     if (Nc) *Nc = h->Nc;
     return AFQMC_OK;

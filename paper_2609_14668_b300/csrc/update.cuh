@@ -44,7 +44,37 @@ struct UpdArgs {
     unsigned long long* n_acc;
     DevStatus* st;
     int precision;                // 0: FP64 flush; 1: split-TF32 tcgen05 flush, FP32 accumulate
+    int pair;                     // 1: G is the real 2Np x 2Np embedding of a complex G (twist)
+    int Np;                       // physical sites (field length); N = 2 Np when pair
 };
+
+// Window of the proposals.  Plain: positions t = 0..nw-1 are the sites c0 + t.
+// Pair mode: a physical flip of site p changes rows p and p + Np of the
+// embedding (Delta is real), i.e. two rank-1 moves; positions 2q and 2q + 1 are
+// the sites c0 + q and c0 + q + Np, so a window holds whole pairs and the
+// positions stay in proposal order.
+__device__ __forceinline__ int win_site(const UpdArgs& a, int c0, int t) {
+    return a.pair ? c0 + (t >> 1) + (t & 1) * a.Np : c0 + t;
+}
+__device__ __forceinline__ int win_pos(const UpdArgs& a, int c0, int site) {
+    if (!a.pair) return site - c0;
+    return site < a.Np ? 2 * (site - c0) : 2 * (site - a.Np - c0) + 1;
+}
+__device__ __forceinline__ int win_len(const UpdArgs& a, int c0) {
+    return a.pair ? 2 * min(a.W >> 1, a.Np - c0) : min(a.W, a.N - c0);
+}
+__device__ __forceinline__ int win_phys(const UpdArgs& a, int c0, int t) {   // physical site of position t
+    return a.pair ? c0 + (t >> 1) : c0 + t;
+}
+
+// 1 / r: hardware reciprocal estimate refined by two Newton steps
+__device__ __forceinline__ double recip_nr(double r) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(r));
+    y = fma(y, fma(-r, y, 1.0), y);
+    y = fma(y, fma(-r, y, 1.0), y);
+    return y;
+}
 
 // ---------------------------------------------------------------------------
 // Split-TF32 flush (precision 1): G -= X Y with X = Xh + Xl, Y = Yh + Yl (each
@@ -254,16 +284,17 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
             int8_t* sw = reinterpret_cast<int8_t*>(od + W); // W field values
             __shared__ int s_found[2];
             __shared__ double s_c[2];
-            const int nw = min(W, N - cursor);
+            const int nw = win_len(a, cursor);
             const int ld = W + 1;
             for (int o = threadIdx.x; o < nw * nw; o += blockDim.x) {
                 const int r = o / nw, c = o - r * nw;
-                Gw[r * ld + c] = (k == 0) ? __ldcg(a.G + (size_t)(cursor + r) * N + cursor + c)
+                Gw[r * ld + c] = (k == 0) ? __ldcg(a.G + (size_t)win_site(a, cursor, r) * N + win_site(a, cursor, c))
                                           : __ldcg(a.Gw + r * W + c);
             }
             for (int t = threadIdx.x; t < nw; t += blockDim.x) {
-                const int sg = a.s[cursor + t];
-                const double u = sm64_uniform(a.key, a.ctr0 + cursor + t);
+                const int ps = win_phys(a, cursor, t);
+                const int sg = a.s[ps];
+                const double u = sm64_uniform(a.key, a.ctr0 + ps);
                 // accept iff u < e^{2 gamma s} r^2  <=>  r^2 > u e^{-2 gamma s}
                 vv[t] = u * (sg > 0 ? a.ef_m : a.ef_p);
                 dd[t] = sg > 0 ? a.dl_p : a.dl_m;
@@ -281,14 +312,30 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                         const double dl = dd[t0];
                         const double r = fma(-dl, Gw[t0 * ld + t0], od[t0]);   // 1 + Delta (1 - G_ii)
                         if (!isfinite(r)) { flag_error(a.st, DERR_NUMERIC, 200); continue; }
+                        if (a.pair) {
+                            if (t0 & 1) {            // second half of an accepted pair
+                                found = t0;
+                                c = dl * recip_nr(r);
+                                break;
+                            }
+                            // r1 r2 = |1 + Delta (1 - G_pp)|^2 of the complex G: r2 from the
+                            // diagonal entry the first move leaves behind (same arithmetic as
+                            // warp 0's update below)
+                            const double c1 = dl * recip_nr(r);
+                            const int q = t0 + 1;
+                            const double g2 = fma(c1 * Gw[q * ld + t0], Gw[t0 * ld + q], Gw[q * ld + q]);
+                            const double r2 = fma(-dl, g2, od[t0]);
+                            if (r * r2 > vv[t0]) {
+                                found = t0;
+                                c = c1;
+                                break;
+                            }
+                            ++t0;                    // rejected: skip the partner too
+                            continue;
+                        }
                         if (r * r > vv[t0]) {
-                            // c = Delta / r: hardware reciprocal estimate + two Newton steps
-                            double y;
-                            asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(r));
-                            y = fma(y, fma(-r, y, 1.0), y);
-                            y = fma(y, fma(-r, y, 1.0), y);
                             found = t0;
-                            c = dl * y;
+                            c = dl * recip_nr(r);
                             break;
                         }
                     }
@@ -301,9 +348,9 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                 if (tf < 0) break;
                 const double c = s_c[slot];
                 if (threadIdx.x == 32) {
-                    a.msite[kk] = cursor + tf;
+                    a.msite[kk] = win_site(a, cursor, tf);
                     a.mcoef[kk] = c;
-                    a.s[cursor + tf] = (int8_t)(-sw[tf]);
+                    if (!a.pair || !(tf & 1)) a.s[win_phys(a, cursor, tf)] = (int8_t)(-sw[tf]);
                 }
                 const int rest = nw - tf - 1;
                 for (int p = (int)threadIdx.x - 32; p >= 0 && p < rest; p += blockDim.x - 32) {
@@ -312,14 +359,24 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                     a.yw[kk * W + q] = -Gw[tf * ld + q];
                 }
                 if (threadIdx.x < 32) {
-                    // warp 0: one diagonal entry per lane, then hand back to thread 0
+                    // warp 0: one diagonal entry per lane (and, in pair mode, the two
+                    // off-diagonal entries inside the pair that starts there: the
+                    // pair decision reads them), then hand back to thread 0
                     const int q = tf + 1 + (int)threadIdx.x;
-                    if (q < nw) Gw[q * ld + q] = fma(c * Gw[q * ld + tf], Gw[tf * ld + q], Gw[q * ld + q]);
+                    if (q < nw) {
+                        Gw[q * ld + q] = fma(c * Gw[q * ld + tf], Gw[tf * ld + q], Gw[q * ld + q]);
+                        if (a.pair && !(q & 1) && q + 1 < nw) {
+                            const int q1 = q + 1;
+                            Gw[q1 * ld + q] = fma(c * Gw[q1 * ld + tf], Gw[tf * ld + q], Gw[q1 * ld + q]);
+                            Gw[q * ld + q1] = fma(c * Gw[q * ld + tf], Gw[tf * ld + q1], Gw[q * ld + q1]);
+                        }
+                    }
                     __syncwarp();
                 } else {
                     for (int o = threadIdx.x - 32; o < rest * rest; o += blockDim.x - 32) {
                         const int q = tf + 1 + o / rest, p = tf + 1 + o % rest;
-                        if (q != p) Gw[q * ld + p] = fma(c * Gw[q * ld + tf], Gw[tf * ld + p], Gw[q * ld + p]);
+                        if (q == p || (a.pair && (q >> 1) == (p >> 1))) continue;   // warp 0's entries
+                        Gw[q * ld + p] = fma(c * Gw[q * ld + tf], Gw[tf * ld + p], Gw[q * ld + p]);
                     }
                 }
                 ++kk;
@@ -329,7 +386,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                 a.ctl[0] = cursor;
                 a.ctl[1] = k;
                 a.ctl[2] = kk;
-                a.ctl[3] = cursor + tstop;
+                a.ctl[3] = cursor + (a.pair ? tstop >> 1 : tstop);
                 if (kk > k) atomicAdd(a.n_acc, (unsigned long long)(kk - k));
             }
         }
@@ -343,7 +400,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
         // window's sites, and the window tables of the new moves.
         if (ka > kb) {
             const int nn = ka - kb;
-            const int nw = c1 > c0 ? min(W, N - c0) : 0;
+            const int nw = c1 > c0 ? win_len(a, c0) : 0;
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
             const int JPB = (N + gridDim.x - 1) / gridDim.x;
             const int jb = blockIdx.x * JPB;
@@ -377,7 +434,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                             dst[q] = (half ? (int)(sYj - upd_smem) : (int)(sXj - upd_smem)) + e;
                         } else if (e < n1 + n2) {
                             const int f = e - n1, p = f / W, t = f - p * W;
-                            if (t < nw) v[q] = __ldcg(srcm + (size_t)p * N + c0 + t);
+                            if (t < nw) v[q] = __ldcg(srcm + (size_t)p * N + win_site(a, c0, t));
                             dst[q] = (half ? (int)(sYw - upd_smem) : (int)(sXw - upd_smem)) + f;
                         } else {
                             const int f = e - n1 - n2;
@@ -394,7 +451,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
             const bool mine = lane < nn;
             const int mm = kb + lane;
             const int im = mine ? __ldcg(a.msite + mm) : c0;
-            const int tm = im - c0;
+            const int tm = win_pos(a, c0, im);
             const double cm = mine ? __ldcg(a.mcoef + mm) : 0.0;
             for (int jj = warp; jj < nj; jj += nwarp) {
                 const int j = jb + jj;
@@ -435,7 +492,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
         }
         if (!grid_barrier(a.st, 2)) break;
         k = ka;
-        const bool done = (c1 >= N);
+        const bool done = (c1 >= (a.pair ? a.Np : N));
         // ------------------------------------------------------------ phase F
         if (k > 0 && (k == nd || done)) {
             if (a.precision == 1) {
@@ -479,16 +536,17 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
         cursor = c1;
         // ------------------------------------------------------------ phase A
         if (k > 0) {
-            const int nw = min(W, N - cursor);
+            const int nw = win_len(a, cursor);
             const int lane = threadIdx.x & 31;
             const int gwarp = gtid >> 5, nwarps = gthreads >> 5;
             for (int e = gwarp; e < nw * nw; e += nwarps) {
                 const int r = e / nw, c = e - r * nw;
+                const int sr = win_site(a, cursor, r), sc = win_site(a, cursor, c);
                 double acc = 0.0;
                 for (int m = lane; m < k; m += 32)
-                    acc = fma(__ldcg(a.Xs + (size_t)m * N + cursor + r), __ldcg(a.Ys + (size_t)m * N + cursor + c), acc);
+                    acc = fma(__ldcg(a.Xs + (size_t)m * N + sr), __ldcg(a.Ys + (size_t)m * N + sc), acc);
                 acc = warp_sum(acc);
-                if (lane == 0) a.Gw[r * W + c] = __ldcg(a.G + (size_t)(cursor + r) * N + cursor + c) - acc;
+                if (lane == 0) a.Gw[r * W + c] = __ldcg(a.G + (size_t)sr * N + sc) - acc;
             }
             if (!grid_barrier(a.st, 4)) break;
         }

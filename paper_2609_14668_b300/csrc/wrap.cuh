@@ -142,20 +142,34 @@ __device__ double2* dft2d(double2* z, double2* t, int VP, const FFTPlan& P, bool
 // matrix with N columns; Op = U^+ blk U.  blk: Nc entries of 4 double2
 // (row-major 2x2 block per k, index l1 + L1*l2).  transpose_out: write
 // out[j*ldo + r] instead of out[r*ldo + j] (then in != out is required).
+//
+// emb != 0 (twisted boundaries, complex operator): the matrix is the real
+// 2N x 2N embedding [[Re X, -Im X], [Im X, Re X]] of a complex X, and each row
+// of length 2N is one complex vector z = row[0:N] + i row[N:2N]; the kernel
+// writes [Re Op z, Im Op z].  For a column of the embedding this is the
+// embedding of Op applied to the complex column; for a row it is the row
+// times the embedding of Op, because every Op used here (e^{+-c dtau K}) is
+// Hermitian.  The diagonal scalings act on both halves.
 __global__ void __launch_bounds__(256) k_rowop(const double* in, double* out,
                                                int nrows, int ldi, int ldo, FFTPlan P,
                                                const double2* __restrict__ blk,
-                                               DiagScale pre, DiagScale post, int transpose_out, int VP) {
+                                               DiagScale pre, DiagScale post, int transpose_out, int VP, int emb) {
     extern __shared__ double2 smem_rowop[];
     const int N = P.N, Nc = P.Nc;
     double2* z = smem_rowop;
     double2* t = smem_rowop + (size_t)VP * N;
-    const int r0 = blockIdx.x * 2 * VP;
-    // load: vector v = row (r0+2v) + i row (r0+2v+1)
+    const int r0 = blockIdx.x * (emb ? VP : 2 * VP);
+    // load: vector v = row (r0+2v) + i row (r0+2v+1), or (emb) the two halves of row r0+v
     for (int o = threadIdx.x; o < VP * N; o += blockDim.x) {
         const int v = o / N, j = o - v * N;
-        const int ra = r0 + 2 * v, rb = ra + 1;
         const double d = pre.at(j);
+        if (emb) {
+            const int r = r0 + v;
+            const double* row = in + (size_t)r * ldi;
+            z[o] = r < nrows ? make_double2(row[j] * d, row[N + j] * d) : make_double2(0.0, 0.0);
+            continue;
+        }
+        const int ra = r0 + 2 * v, rb = ra + 1;
         const double xa = ra < nrows ? in[(size_t)ra * ldi + j] * d : 0.0;
         const double xb = rb < nrows ? in[(size_t)rb * ldi + j] * d : 0.0;
         z[o] = make_double2(xa, xb);
@@ -175,6 +189,29 @@ __global__ void __launch_bounds__(256) k_rowop(const double* in, double* out,
     double2* w = (y == z) ? t : z;
     double2* res = dft2d(y, w, VP, P, true);
     const double inv = 1.0 / (double)Nc;
+    if (emb) {
+        if (!transpose_out) {
+            for (int o = threadIdx.x; o < VP * N; o += blockDim.x) {
+                const int v = o / N, j = o - v * N;
+                const int r = r0 + v;
+                if (r >= nrows) continue;
+                const double d = post.at(j) * inv;
+                const double2 q = res[o];
+                out[(size_t)r * ldo + j] = q.x * d;
+                out[(size_t)r * ldo + N + j] = q.y * d;
+            }
+        } else {
+            for (int o = threadIdx.x; o < VP * 2 * N; o += blockDim.x) {
+                const int j2 = o / VP, v = o - j2 * VP;
+                const int r = r0 + v;
+                if (r >= nrows) continue;
+                const int j = j2 < N ? j2 : j2 - N;
+                const double2 q = res[(size_t)v * N + j];
+                out[(size_t)j2 * ldo + r] = (j2 < N ? q.x : q.y) * post.at(j) * inv;
+            }
+        }
+        return;
+    }
     if (!transpose_out) {
         for (int o = threadIdx.x; o < VP * N; o += blockDim.x) {
             const int v = o / N, j = o - v * N;
