@@ -80,6 +80,8 @@ typedef struct {
     int32_t measure;       /* 1: accumulate observables at every recomputation of G in a sweep */
     int32_t chain;         /* chain index: selects the random stream */
     int32_t device;        /* CUDA device ordinal */
+    int32_t update_ctas;   /* CTAs of the cooperative slice kernel; 0 = one per SM.  A tuning
+                              knob only (results do not depend on it); see afqmc_batch_autotune */
     uint64_t seed;         /* random seed; also draws the initial field */
 } afqmc_params;
 
@@ -223,6 +225,43 @@ afqmc_status afqmc_update_slice_noalloc(double* G_dev, int8_t* s_dev, int32_t N,
                                         int32_t pass, uint64_t sweep_index, double U, double dtau,
                                         int32_t n_delay, uint64_t seed, int32_t chain, void* cuda_stream,
                                         int32_t* n_accepted);
+
+/* ---------------------------------------------------------------- batches
+ * Independent chains (any mix of L, twist, seed; e.g. twist averaging over a
+ * grid of boundary phases, Sec. III.C) run together on one device.  Each
+ * chain keeps its own handle, stream and state; one sweep of the whole batch
+ * is a single CUDA graph (captured on the first sweep: every chain's launch
+ * sequence on its own branch), so the chains' kernels overlap on the GPU and
+ * the host issues one launch per batched sweep.  Every chain computes exactly
+ * what afqmc_sweep computes for it (same random numbers, same decisions). */
+typedef struct afqmc_batch afqmc_batch;
+
+/* Create n >= 1 chains from params[0..n-1] (all on params[0].device).
+ * Per-launch timing is not available on batch chains. */
+afqmc_status afqmc_batch_create(const afqmc_params* params, int32_t n, afqmc_batch** out);
+afqmc_status afqmc_batch_destroy(afqmc_batch* b);
+
+/* n_sweeps sweeps of every chain (one graph launch each); total (may be NULL)
+ * sums proposed/accepted/launches over the chains, max_stab_drift is the max. */
+afqmc_status afqmc_batch_sweep(afqmc_batch* b, int32_t n_sweeps, afqmc_sweep_stats* total);
+
+/* Chain i of the batch (0 <= i < n), owned by the batch: use it for fields,
+ * observables and G between batched sweeps; do not destroy it.  NULL if out of range. */
+afqmc_handle* afqmc_batch_chain(afqmc_batch* b, int32_t i);
+
+/* Autotuner: for the chains described by params[0..n-1], builds the batch for
+ * every candidate (n_delays[a], ctas[c]) (ctas 0 = one CTA per SM), runs one
+ * warm-up and n_timed timed batched sweeps, and returns the pair with the
+ * highest total proposals per second (and that rate).  The delay rank and the
+ * slice kernel's grid change only the speed, never the Markov chain (the
+ * delayed update is exact algebra).  Errors from a candidate abort the search. */
+afqmc_status afqmc_batch_autotune(const afqmc_params* params, int32_t n, const int32_t* n_delays, int32_t n_nd,
+                                  const int32_t* ctas, int32_t n_ctas, int32_t n_timed, int32_t* best_n_delay,
+                                  int32_t* best_ctas, double* best_rate);
+
+/* Message of the last failed batch call on b (never NULL); b == NULL: the last
+ * failure of afqmc_batch_create or afqmc_batch_autotune on this thread. */
+const char* afqmc_batch_last_error(const afqmc_batch* b);
 
 /* Sizes of the handle: N (physical sites 2 Nc), M, Nc. */
 afqmc_status afqmc_dims(const afqmc_handle* h, int32_t* N, int32_t* M, int32_t* Nc);

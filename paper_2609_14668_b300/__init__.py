@@ -28,7 +28,8 @@ class afqmc_params(ctypes.Structure):
                 ("beta", ctypes.c_double), ("dtau", ctypes.c_double), ("theta1", ctypes.c_double),
                 ("theta2", ctypes.c_double), ("hs_channel", ctypes.c_int32), ("n_delay", ctypes.c_int32),
                 ("n_stab", ctypes.c_int32), ("precision", ctypes.c_int32), ("measure", ctypes.c_int32),
-                ("chain", ctypes.c_int32), ("device", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("chain", ctypes.c_int32), ("device", ctypes.c_int32), ("update_ctas", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
 
 
 class afqmc_sweep_stats(ctypes.Structure):
@@ -76,6 +77,12 @@ _SIGS = {
                                     ctypes.c_uint64, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
                                     ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p, _P(ctypes.c_int32)]),
     "afqmc_get_timing": ([_H, _P(afqmc_timing)]),
+    "afqmc_batch_create": ([_P(afqmc_params), ctypes.c_int32, _P(_H)]),
+    "afqmc_batch_destroy": ([_H]),
+    "afqmc_batch_sweep": ([_H, ctypes.c_int32, _P(afqmc_sweep_stats)]),
+    "afqmc_batch_autotune": ([_P(afqmc_params), ctypes.c_int32, _P(ctypes.c_int32), ctypes.c_int32,
+                              _P(ctypes.c_int32), ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_int32),
+                              _P(ctypes.c_int32), _DP]),
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -83,8 +90,12 @@ for _name, _args in _SIGS.items():
     _f.restype = ctypes.c_int
 _lib.afqmc_last_error.argtypes = [_H]
 _lib.afqmc_last_error.restype = ctypes.c_char_p
+_lib.afqmc_batch_last_error.argtypes = [_H]
+_lib.afqmc_batch_last_error.restype = ctypes.c_char_p
+_lib.afqmc_batch_chain.argtypes = [_H, ctypes.c_int32]
+_lib.afqmc_batch_chain.restype = _H
 
-EXPORTED = sorted(list(_SIGS) + ["afqmc_last_error"])
+EXPORTED = sorted(list(_SIGS) + ["afqmc_last_error", "afqmc_batch_last_error", "afqmc_batch_chain"])
 
 
 class AfqmcError(RuntimeError):
@@ -242,21 +253,102 @@ def afqmc_update_slice_noalloc(G_dev_ptr, s_dev_ptr, N, M, slice_, pas, sweep_in
     return n.value
 
 
+def _check_batch(code, b):
+    if code != 0:
+        msg = _lib.afqmc_batch_last_error(b)
+        raise AfqmcError(code, msg.decode() if msg else "")
+
+
+def afqmc_batch_create(params_list):
+    arr = (afqmc_params * len(params_list))(*params_list)
+    b = _H()
+    _check_batch(_lib.afqmc_batch_create(arr, len(params_list), ctypes.byref(b)), None)
+    for i, p in enumerate(params_list):
+        if p.theta1 != 0.0 or p.theta2 != 0.0:
+            _COMPLEX.add(ctypes.cast(_lib.afqmc_batch_chain(b, i), ctypes.c_void_p).value)
+    return b
+
+
+def afqmc_batch_chain(b, i):
+    h = _lib.afqmc_batch_chain(b, i)
+    if not h:
+        raise AfqmcError(1, f"no chain {i} in the batch")
+    return _H(h)
+
+
+def afqmc_batch_destroy(b, n=0):
+    for i in range(n):
+        _COMPLEX.discard(ctypes.cast(_lib.afqmc_batch_chain(b, i), ctypes.c_void_p).value)
+    _lib.afqmc_batch_destroy(b)
+
+
+def afqmc_batch_sweep(b, n_sweeps=1):
+    st = afqmc_sweep_stats()
+    _check_batch(_lib.afqmc_batch_sweep(b, n_sweeps, ctypes.byref(st)), b)
+    return st
+
+
+def afqmc_batch_autotune(params_list, n_delays, ctas, n_timed=1):
+    arr = (afqmc_params * len(params_list))(*params_list)
+    nd = (ctypes.c_int32 * len(n_delays))(*n_delays)
+    cc = (ctypes.c_int32 * len(ctas))(*ctas)
+    bn, bc, br = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check_batch(_lib.afqmc_batch_autotune(arr, len(params_list), nd, len(n_delays), cc, len(ctas), n_timed,
+                                           ctypes.byref(bn), ctypes.byref(bc), ctypes.byref(br)), None)
+    return bn.value, bc.value, br.value
+
+
+def afqmc_batch_last_error(b=None):
+    m = _lib.afqmc_batch_last_error(b)
+    return m.decode() if m else ""
+
+
 def afqmc_last_error(h=None):
     m = _lib.afqmc_last_error(h)
     return m.decode() if m else ""
 
 
 def make_params(L, beta, dtau, U, n_delay, n_stab, t=1.0, seed=0, chain=0, measure=0, device=0, L2=None,
-                precision=0, theta=(0.0, 0.0)):
+                precision=0, theta=(0.0, 0.0), update_ctas=0):
     return afqmc_params(L1=L, L2=L if L2 is None else L2, t=t, U=U, beta=beta, dtau=dtau,
                         theta1=float(theta[0]), theta2=float(theta[1]),
                         hs_channel=0, n_delay=n_delay, n_stab=n_stab, precision=precision, measure=measure,
-                        chain=chain, device=device, seed=seed)
+                        chain=chain, device=device, update_ctas=update_ctas, seed=seed)
+
+
+class Batch:
+    """Independent chains swept together, one CUDA graph launch per batched sweep."""
+
+    def __init__(self, params_list):
+        self.params = list(params_list)
+        self.b = afqmc_batch_create(self.params)
+        self.chains = []
+        for i, p in enumerate(self.params):
+            c = Chain.__new__(Chain)
+            c.params, c.h, c.borrowed = p, afqmc_batch_chain(self.b, i), True
+            c.N, c.M, c.Nc = afqmc_dims(c.h)
+            self.chains.append(c)
+
+    def sweep(self, n=1):
+        return afqmc_batch_sweep(self.b, n)
+
+    def close(self):
+        if self.b:
+            for c in self.chains:
+                c.h = None
+            afqmc_batch_destroy(self.b, len(self.params))
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Chain:
     """One Markov chain on the GPU (owns an afqmc handle)."""
+    borrowed = False
 
     def __init__(self, params, stream=None):
         self.params = params
@@ -264,9 +356,9 @@ class Chain:
         self.N, self.M, self.Nc = afqmc_dims(self.h)
 
     def close(self):
-        if self.h:
+        if self.h and not self.borrowed:
             afqmc_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:

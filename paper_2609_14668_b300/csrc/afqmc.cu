@@ -60,9 +60,12 @@ struct afqmc_handle {
     double gamma = 0.0, egp = 1.0, egm = 1.0;      // e^{gamma}, e^{-gamma}
     double dl_p = 0.0, dl_m = 0.0, ef_p = 1.0, ef_m = 1.0;
     uint64_t key = 0, sweep_index = 0;
+    unsigned long long* d_sweep = nullptr;   // device copy of sweep_index (read by the slice kernel)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int sms = 0;
+    int upd_grid = 0;              // CTAs of the cooperative slice kernel
+    bool in_batch = false;         // owned by an afqmc_batch (no per-launch timing)
     bool broken = false;
     std::string err;
     // device memory
@@ -369,7 +372,9 @@ void half_step(afqmc_handle* h, const double* A, double* out) {
     launch_rowop(h, T, out, h->N, OP_EH, no_scale(), no_scale(), true);
 }
 
-void update_slice(afqmc_handle* h, double* G, int l, int pass, uint64_t sweep) {
+// sweep < 0: the sweep number is the device-resident one (sweep path, graph
+// replays); otherwise the given number (test hooks).
+void update_slice(afqmc_handle* h, double* G, int l, int pass, int64_t sweep) {
     UpdArgs a{};
     a.G = G; a.N = h->N; a.Xs = h->Xs; a.Ys = h->Ys; a.msite = h->msite; a.mcoef = h->mcoef;
     a.xw = h->xw; a.yw = h->yw; a.Gw = h->Gw; a.ctl = h->ctl;
@@ -378,13 +383,16 @@ void update_slice(afqmc_handle* h, double* G, int l, int pass, uint64_t sweep) {
     a.pair = h->cplx; a.Np = h->Np;
     a.dl_p = h->dl_p; a.dl_m = h->dl_m; a.ef_p = h->ef_p; a.ef_m = h->ef_m;
     a.key = h->key;
-    a.ctr0 = ((sweep * 2 + (uint64_t)pass) * (uint64_t)h->M + (uint64_t)(l - 1)) * (uint64_t)h->Np + 1;
+    a.ctr_stride = 2ull * (uint64_t)h->M * (uint64_t)h->Np;
+    a.ctr0 = ((uint64_t)pass * (uint64_t)h->M + (uint64_t)(l - 1)) * (uint64_t)h->Np + 1;
+    if (sweep < 0) a.sweep_dev = h->d_sweep;
+    else a.ctr0 += (uint64_t)sweep * a.ctr_stride;
     a.n_acc = h->n_acc; a.st = h->st;
     a.precision = h->p.precision;
-    const size_t smem = update_smem(h->W, h->nd, h->p.precision, h->N, h->sms);
+    const size_t smem = update_smem(h->W, h->nd, h->p.precision, h->N, h->upd_grid);
     void* args[] = {&a};
     Scope sc(h, AFQMC_K_UPDATE);
-    CK(cudaLaunchCooperativeKernel((void*)k_update_slice, h->sms, UPD_THREADS, args, smem, h->stream));
+    CK(cudaLaunchCooperativeKernel((void*)k_update_slice, h->upd_grid, UPD_THREADS, args, smem, h->stream));
 }
 
 void measure(afqmc_handle* h, const double* G, bool accumulate) {
@@ -447,7 +455,7 @@ void sweep_once(afqmc_handle* h) {
     const int M = h->M, ns = h->ns;
     for (int l = 1; l <= M; ++l) {
         wrap(h, h->G, l, +1);
-        update_slice(h, h->G, l, 0, h->sweep_index);
+        update_slice(h, h->G, l, 0, -1);
         if (l % ns == 0) {
             const int c = l / ns;
             udt_extend(h, h->Rst[c - 1], h->Rst[c], (c - 1) * ns + 1, c * ns, true);
@@ -455,7 +463,7 @@ void sweep_once(afqmc_handle* h) {
         }
     }
     for (int l = M; l >= 1; --l) {
-        update_slice(h, h->G, l, 1, h->sweep_index);
+        update_slice(h, h->G, l, 1, -1);
         wrap(h, h->G, l, -1);
         if ((l - 1) % ns == 0) {
             const int c = (l - 1) / ns;
@@ -463,6 +471,8 @@ void sweep_once(afqmc_handle* h) {
             recompute(h, c);
         }
     }
+    { Scope sc(h, AFQMC_K_MISC); k_add_u64<<<1, 1, 0, h->stream>>>(h->d_sweep, 1ull); }
+    CK(cudaGetLastError());
     h->sweep_index += 1;
 }
 
@@ -584,6 +594,7 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
     if (M < 1 || std::fabs(M * P.dtau - P.beta) > 1e-9) return bad("beta must be an integer multiple of dtau");
     if (P.n_stab < 1 || M % P.n_stab) return bad("n_stab must divide M = beta/dtau");
     if (P.n_delay < 1 || P.n_delay > 256) return bad("n_delay must be in [1, 256]");
+    if (P.update_ctas < 0) return bad("update_ctas must be >= 0");
     auto* h = new afqmc_handle();
     try {
         h->p = P;
@@ -647,11 +658,13 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         for (const void* f : {(const void*)k_apply_qt, (const void*)k_form_q, (const void*)k_backsolve,
                               (const void*)k_fwdsolve_perm})
             CK(raise_smem_limit(f, cpb_smem(N)));
-        const size_t usmem = update_smem(h->W, h->nd, P.precision, N, h->sms);
+        h->upd_grid = P.update_ctas > 0 ? P.update_ctas : h->sms;
+        const size_t usmem = update_smem(h->W, h->nd, P.precision, N, h->upd_grid);
         CK(raise_smem_limit((const void*)k_update_slice, usmem));
         int occ = 0;
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_slice, UPD_THREADS, usmem));
         if (occ < 1) throw CudaFail{AFQMC_E_INVALID, "update kernel does not fit on an SM"};
+        if (h->upd_grid > occ * h->sms) throw CudaFail{AFQMC_E_INVALID, "update_ctas exceeds the co-resident CTAs of the device"};
         {
             const int qg = std::min(h->sms, N);
             const size_t qs = sizeof(double) * (size_t)N * (1 + (N + qg - 1) / qg);
@@ -690,6 +703,8 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         CK(cudaMemset(h->st, 0, sizeof(DevStatus)));
         h->n_acc = h->dalloc<unsigned long long>(1);
         h->drift = h->dalloc<unsigned long long>(1);
+        h->d_sweep = h->dalloc<unsigned long long>(1);
+        CK(cudaMemset(h->d_sweep, 0, sizeof(unsigned long long)));
         h->czz = h->dalloc<double>(Nc);
         h->hab = h->dalloc<double>((size_t)8 * Nc);
         h->obs_now = h->dalloc<double>(OBS_SCALARS);
@@ -760,6 +775,7 @@ afqmc_status afqmc_set_field(afqmc_handle* h, const int8_t* s, uint64_t sweep_in
         if (s[o] != 1 && s[o] != -1) { h->err = "field entries must be +1 or -1"; return AFQMC_E_INVALID; }
     CK(cudaMemcpyAsync(h->field, s, len, cudaMemcpyHostToDevice, h->stream));
     h->sweep_index = sweep_index;
+    CK(cudaMemcpyAsync(h->d_sweep, &h->sweep_index, sizeof(unsigned long long), cudaMemcpyHostToDevice, h->stream));
     init_chain(h);
     return check_device(h);
     API_END(h)
@@ -875,7 +891,7 @@ afqmc_status afqmc_update_slice(afqmc_handle* h, int32_t slice, int32_t pass, ui
     double* d = h->Wk[5];
     from_host(h, G, d, h->Wk[4]);
     CK(cudaMemsetAsync(h->n_acc, 0, sizeof(unsigned long long), h->stream));
-    update_slice(h, d, slice, pass, sweep_index);
+    update_slice(h, d, slice, pass, (int64_t)sweep_index);
     unsigned long long acc = 0;
     to_host(h, d, G, h->Wk[4]);
     CK(cudaMemcpyAsync(&acc, h->n_acc, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
@@ -904,6 +920,7 @@ afqmc_status afqmc_det_ratio(afqmc_handle* h, int32_t slice, int32_t site, doubl
 
 afqmc_status afqmc_set_timing(afqmc_handle* h, int32_t family_mask) {
     API_BEGIN(h)
+    if (h->in_batch && family_mask) { h->err = "per-launch timing is not available on batch chains"; return AFQMC_E_INVALID; }
     if (family_mask < 0 || family_mask > AFQMC_TIMING_ALL) { h->err = "timing mask outside the kernel families"; return AFQMC_E_INVALID; }
     flush_timing(h);
     h->timing = family_mask;
@@ -994,6 +1011,210 @@ afqmc_status afqmc_update_slice_noalloc(double* G_dev, int8_t* s_dev, int32_t N,
     if (ds.err != 0) { g_create_error = "afqmc_update_slice_noalloc: device error"; return AFQMC_E_CUDA; }
     if (n_accepted) *n_accepted = (int32_t)acc;
     return AFQMC_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== batches
+struct afqmc_batch {
+    std::vector<afqmc_handle*> chains;
+    cudaStream_t stream = nullptr;          // the graph is launched here
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t launches_per_sweep = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_batch_error;
+
+void batch_free(afqmc_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto e : b->join) if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (auto* h : b->chains) afqmc_destroy(h);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+// One sweep of every chain captured into one graph: fork from the batch
+// stream to every chain's stream, each chain's launch sequence on its own
+// branch, join back.
+void batch_capture(afqmc_batch* b) {
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    uint64_t l0 = 0;
+    try {
+        CK(cudaEventRecord(b->fork, b->stream));
+        for (size_t i = 0; i < b->chains.size(); ++i) {
+            afqmc_handle* h = b->chains[i];
+            CK(cudaStreamWaitEvent(h->stream, b->fork, 0));
+            l0 = h->launches;
+            sweep_once(h);
+            b->launches_per_sweep += h->launches - l0;
+            h->sweep_index -= 1;              // advanced on every replay instead
+            CK(cudaEventRecord(b->join[i], h->stream));
+            CK(cudaStreamWaitEvent(b->stream, b->join[i], 0));
+        }
+    } catch (...) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(b->stream, &g);
+        if (g) cudaGraphDestroy(g);
+        b->launches_per_sweep = 0;
+        throw;
+    }
+    CK(cudaStreamEndCapture(b->stream, &b->graph));
+    CK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+}
+
+afqmc_status batch_sweep_impl(afqmc_batch* b, int32_t n_sweeps, afqmc_sweep_stats* total) {
+    for (auto* h : b->chains) {
+        if (h->broken) { b->err = "chain unusable after an earlier error: " + h->err; return AFQMC_E_STATE; }
+        CK(cudaStreamSynchronize(h->stream));     // work issued on the chain's own stream comes first
+        CK(cudaMemsetAsync(h->n_acc, 0, sizeof(unsigned long long), b->stream));
+        CK(cudaMemsetAsync(h->drift, 0, sizeof(unsigned long long), b->stream));
+    }
+    if (!b->exec && n_sweeps > 0) batch_capture(b);
+    for (int w = 0; w < n_sweeps; ++w) {
+        CK(cudaGraphLaunch(b->exec, b->stream));
+        for (auto* h : b->chains) h->sweep_index += 1;
+    }
+    std::vector<unsigned long long> acc(b->chains.size()), dr(b->chains.size());
+    for (size_t i = 0; i < b->chains.size(); ++i) {
+        CK(cudaMemcpyAsync(&acc[i], b->chains[i]->n_acc, sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->stream));
+        CK(cudaMemcpyAsync(&dr[i], b->chains[i]->drift, sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->stream));
+    }
+    CK(cudaStreamSynchronize(b->stream));
+    afqmc_status worst = AFQMC_OK;
+    afqmc_sweep_stats t{};
+    for (size_t i = 0; i < b->chains.size(); ++i) {
+        afqmc_handle* h = b->chains[i];
+        afqmc_status s = check_device(h);
+        if (s != AFQMC_OK && worst == AFQMC_OK) { worst = s; b->err = "chain " + std::to_string(i) + ": " + h->err; }
+        t.proposed += (uint64_t)n_sweeps * 2ull * (uint64_t)h->Np * (uint64_t)h->M;
+        t.accepted += h->cplx ? acc[i] / 2 : acc[i];
+        double d;
+        std::memcpy(&d, &dr[i], sizeof(d));
+        t.max_stab_drift = std::max(t.max_stab_drift, d);
+    }
+    t.launches = (uint64_t)n_sweeps * b->launches_per_sweep;
+    if (total) *total = t;
+    return worst;
+}
+
+}  // namespace
+
+extern "C" {
+
+afqmc_status afqmc_batch_create(const afqmc_params* params, int32_t n, afqmc_batch** out) {
+    if (out) *out = nullptr;
+    if (!params || !out || n < 1) { g_batch_error = "null argument or n < 1"; return AFQMC_E_INVALID; }
+    for (int i = 1; i < n; ++i)
+        if (params[i].device != params[0].device) { g_batch_error = "all chains of a batch must use one device"; return AFQMC_E_INVALID; }
+    auto* b = new afqmc_batch();
+    try {
+        CK(cudaSetDevice(params[0].device));
+        CK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+        for (int i = 0; i < n; ++i) {
+            afqmc_handle* h = nullptr;
+            afqmc_status s = afqmc_create(&params[i], nullptr, &h);
+            if (s != AFQMC_OK) {
+                g_batch_error = "chain " + std::to_string(i) + ": " + g_create_error;
+                batch_free(b);
+                return s;
+            }
+            h->in_batch = true;
+            b->chains.push_back(h);
+            cudaEvent_t e;
+            CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            b->join.push_back(e);
+        }
+    } catch (const CudaFail& f) {
+        g_batch_error = f.msg;
+        batch_free(b);
+        return f.code;
+    }
+    *out = b;
+    return AFQMC_OK;
+}
+
+afqmc_status afqmc_batch_destroy(afqmc_batch* b) {
+    batch_free(b);
+    return AFQMC_OK;
+}
+
+afqmc_status afqmc_batch_sweep(afqmc_batch* b, int32_t n_sweeps, afqmc_sweep_stats* total) {
+    if (!b) return AFQMC_E_INVALID;
+    if (n_sweeps < 0) { b->err = "n_sweeps < 0"; return AFQMC_E_INVALID; }
+    try {
+        return batch_sweep_impl(b, n_sweeps, total);
+    } catch (const CudaFail& f) {
+        b->err = f.msg;
+        for (auto* h : b->chains) set_error(h, f.code, f.msg);
+        return f.code;
+    }
+}
+
+afqmc_handle* afqmc_batch_chain(afqmc_batch* b, int32_t i) {
+    if (!b || i < 0 || i >= (int32_t)b->chains.size()) return nullptr;
+    return b->chains[i];
+}
+
+afqmc_status afqmc_batch_autotune(const afqmc_params* params, int32_t n, const int32_t* n_delays, int32_t n_nd,
+                                  const int32_t* ctas, int32_t n_ctas, int32_t n_timed, int32_t* best_n_delay,
+                                  int32_t* best_ctas, double* best_rate) {
+    if (!params || n < 1 || !n_delays || n_nd < 1 || !ctas || n_ctas < 1 || n_timed < 1) {
+        g_batch_error = "bad autotune arguments";
+        return AFQMC_E_INVALID;
+    }
+    std::vector<afqmc_params> ps(params, params + n);
+    double best = -1.0;
+    int bn = 0, bc = 0;
+    for (int a = 0; a < n_nd; ++a)
+        for (int c = 0; c < n_ctas; ++c) {
+            for (auto& p : ps) { p.n_delay = n_delays[a]; p.update_ctas = ctas[c]; }
+            afqmc_batch* b = nullptr;
+            afqmc_status s = afqmc_batch_create(ps.data(), n, &b);
+            if (s != AFQMC_OK) return s;
+            afqmc_sweep_stats st{};
+            s = afqmc_batch_sweep(b, 1, &st);
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            float ms = 0.0f;
+            if (s == AFQMC_OK) {
+                cudaEventCreate(&e0);
+                cudaEventCreate(&e1);
+                cudaEventRecord(e0, b->stream);
+                s = afqmc_batch_sweep(b, n_timed, &st);
+                cudaEventRecord(e1, b->stream);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+            }
+            if (s != AFQMC_OK) {
+                g_batch_error = "candidate (n_delay " + std::to_string(n_delays[a]) + ", ctas " +
+                                std::to_string(ctas[c]) + "): " + b->err;
+                batch_free(b);
+                return s;
+            }
+            const double rate = (double)st.proposed / (ms * 1e-3);
+            if (rate > best) { best = rate; bn = n_delays[a]; bc = ctas[c]; }
+            batch_free(b);
+        }
+    if (best_n_delay) *best_n_delay = bn;
+    if (best_ctas) *best_ctas = bc;
+    if (best_rate) *best_rate = best;
+    return AFQMC_OK;
+}
+
+const char* afqmc_batch_last_error(const afqmc_batch* b) {
+    return b ? b->err.c_str() : g_batch_error.c_str();
 }
 
 afqmc_status afqmc_dims(const afqmc_handle* h, int32_t* N, int32_t* M, int32_t* Nc) {

@@ -191,6 +191,9 @@ __global__ void k_extract(const double* __restrict__ E, double2* X, int N) {
     X[o] = make_double2(E[i * ld + j], E[(N + i) * ld + j]);
 }
 
+// *p += v (a device-resident counter advanced inside the launch sequence)
+__global__ void k_add_u64(unsigned long long* p, unsigned long long v) { *p += v; }
+
 // Initial field from the counter-based stream: s = +1 iff u(key, 2^62 + l*N + i + 1) < 1/2.
 __global__ void k_init_field(int8_t* s, int M, int N, uint64_t key) {
     const size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x;

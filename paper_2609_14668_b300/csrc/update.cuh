@@ -40,7 +40,9 @@ struct UpdArgs {
     int nd, W;
     double dl_p, dl_m;            // Delta for s = +1, -1
     double ef_p, ef_m;            // e^{2 gamma s} for s = +1, -1
-    uint64_t key, ctr0;           // random number of site i is u(key, ctr0 + i)
+    uint64_t key, ctr0;           // random number of site i is u(key, ctr0 + sweep * ctr_stride + i)
+    const unsigned long long* sweep_dev;   // device-resident sweep number (nullptr: 0)
+    uint64_t ctr_stride;
     unsigned long long* n_acc;
     DevStatus* st;
     int precision;                // 0: FP64 flush; 1: split-TF32 tcgen05 flush, FP32 accumulate
@@ -269,6 +271,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
         tmem = s_tmem;
         mbar = smem_u32(&s_mbar);
     }
+    const uint64_t ctr0 = a.ctr0 + (a.sweep_dev ? (uint64_t)__ldcg(a.sweep_dev) * a.ctr_stride : 0ull);
     int cursor = 0, k = 0;
     for (;;) {
         // ------------------------------------------------------------ phase B
@@ -294,7 +297,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
             for (int t = threadIdx.x; t < nw; t += blockDim.x) {
                 const int ps = win_phys(a, cursor, t);
                 const int sg = a.s[ps];
-                const double u = sm64_uniform(a.key, a.ctr0 + ps);
+                const double u = sm64_uniform(a.key, ctr0 + ps);
                 // accept iff u < e^{2 gamma s} r^2  <=>  r^2 > u e^{-2 gamma s}
                 vv[t] = u * (sg > 0 ? a.ef_m : a.ef_p);
                 dd[t] = sg > 0 ? a.dl_p : a.dl_m;

@@ -23,6 +23,26 @@ WORKLOADS = {
 }
 
 
+# Batched twist-averaging workload: 64 independent chains of uneven size, each
+# size on the uniform 4 x 4 grid of twist angles theta in {0, 1/4, 1/2, 3/4}^2
+# (boundary phases 2 pi theta), beta t = L, U/t = 3.73, FP64.  64 chains over
+# 3 sizes x 16 twists: 32 chains at L = 6 (two seeds per twist), 16 at L = 9,
+# 16 at L = 12.
+BATCHED = dict(sizes=((6, 2), (9, 1), (12, 1)), twists=4, dtau=0.1, U=3.73, n_stab=10)
+
+
+def batched_chains():
+    """(L, beta, theta, replica) of every chain of the batched workload."""
+    out = []
+    g = BATCHED["twists"]
+    for L, reps in BATCHED["sizes"]:
+        for a in range(g):
+            for b in range(g):
+                for r in range(reps):
+                    out.append((L, float(L), (a / g, b / g), r))
+    return out
+
+
 def n_slices(beta, dtau):
     m = int(round(beta / dtau))
     if abs(m * dtau - beta) > 1e-9:
