@@ -263,6 +263,79 @@ afqmc_status afqmc_batch_autotune(const afqmc_params* params, int32_t n, const i
  * failure of afqmc_batch_create or afqmc_batch_autotune on this thread. */
 const char* afqmc_batch_last_error(const afqmc_batch* b);
 
+/* ---------------------------------------------------------------- learned block proposals
+ * Not in the paper.  A small network proposes new values for a block of the
+ * Ising field (b x b unit cells, both sublattices, T consecutive slices) from
+ * the field around it (h cells and ht slices of context on every side, the
+ * block itself masked); the chain accepts the proposal by Metropolis-Hastings
+ * with the exact weight ratio W(X')/W(X) (the slice kernel flips the block's
+ * changed sites one after the other and multiplies their ratios, Eq. DRatio)
+ * and the proposal ratio q(s|x)/q(s'|x), so the stationary distribution stays
+ * that of Eq. ConfgWeight whatever the network has learned.
+ *
+ * Network: z = W2 tanh(W1 x + b1) + b2 in FP32, x the context (+1/-1, 0 on the
+ * block), one logit per block entry, q(s'|x) = prod_i sigmoid(s'_i z_i).
+ * Orders: context ((t*W + w2)*W + w1)*2 + sub with W = b + 2h; block
+ * ((t*b + c2)*b + c1)*2 + sub.  Parameters, one FP32 vector:
+ * [W1 (H x Din, row-major) | b1 (H) | W2 (Dout x H) | b2 (Dout)]. */
+typedef struct afqmc_net afqmc_net;
+
+/* New network with seeded random weights on `device`. */
+afqmc_status afqmc_net_create(int32_t b, int32_t T, int32_t h, int32_t ht, int32_t hidden, uint64_t seed,
+                              int32_t device, afqmc_net** out);
+afqmc_status afqmc_net_destroy(afqmc_net* net);
+
+/* dims[0..3] = Din, H, Dout, number of parameters. */
+afqmc_status afqmc_net_dims(const afqmc_net* net, int32_t dims[4]);
+afqmc_status afqmc_net_get_params(afqmc_net* net, float* host);
+afqmc_status afqmc_net_set_params(afqmc_net* net, const float* host);   /* also resets the Adam state */
+
+/* Contexts X (B x Din) and block values S (B x Dout) of B blocks of host field
+ * configurations (n_cfg x M x 2 L1 L2 int8) at pos[4q..4q+3] = (configuration,
+ * l0, o1, o2), as the training and the block pass build them (test hook). */
+afqmc_status afqmc_net_inputs(afqmc_net* net, const int8_t* fields, int32_t n_cfg, int32_t L1, int32_t L2, int32_t M,
+                              const int32_t* pos, int32_t B, float* X, float* S);
+
+/* Logits Z (B x Dout) of contexts X (B x Din), host buffers (test hook). */
+afqmc_status afqmc_net_forward(afqmc_net* net, const float* X, int32_t B, float* Z);
+
+/* Gradient (n_params, host) of the mean loss -sum_i log sigmoid(s_i z_i) over
+ * the batch of contexts X (B x Din) and block values S (B x Dout, +1/-1), and
+ * the loss (test hook; no update). */
+afqmc_status afqmc_net_gradient(afqmc_net* net, const float* X, const float* S, int32_t B, float* grad, double* loss);
+
+/* Train on the GPU: n_cfg field configurations (host, n_cfg x M x 2 L1 L2 int8,
+ * e.g. taken from a chain of the plain sampler); each of n_steps Adam steps
+ * (learning rate lr) uses `batch` blocks at random positions (configuration,
+ * slice, cell offset) drawn from `seed`.  *loss: mean loss of the last step. */
+afqmc_status afqmc_net_train(afqmc_net* net, const int8_t* fields, int32_t n_cfg, int32_t L1, int32_t L2, int32_t M,
+                             int32_t n_steps, int32_t batch, float lr, uint64_t seed, double* loss);
+
+typedef struct {
+    uint64_t proposed;      /* block proposals */
+    uint64_t accepted;      /* accepted block moves */
+    uint64_t flipped;       /* field entries changed by accepted moves */
+    double max_stab_drift;  /* max |G_wrapped - G_recomputed| over the pass */
+} afqmc_block_stats;
+
+/* One block pass of the chain: for every window of T slices (l0 = 1, 1+T, ...)
+ * and every block offset (o1, o2 on the b-grid), propose with the network and
+ * accept or reject (Metropolis-Hastings, exact ratios); G is recomputed from
+ * the stacks every n_stab slices and at the end of the pass, where the chain
+ * is back at slice 0 as after a sweep.  Requires a periodic (real) chain,
+ * T | n_stab and b | L1, L2.  Random numbers: a stream of the chain's key
+ * separate from the sweeps', indexed by the pass number. */
+afqmc_status afqmc_block_sweep(afqmc_handle* h, afqmc_net* net, afqmc_block_stats* stats);
+
+/* Slice update in forced mode (test hook): flip exactly the sites of slice l
+ * with mask[i] != 0 (host, N int8) on a given G (host, N*N, in/out), updating
+ * the handle's field; *logR = sum over the flips of log R = 2 gamma s + log r^2. */
+afqmc_status afqmc_force_slice(afqmc_handle* h, int32_t slice, const int8_t* mask, double* G, double* logR);
+
+/* Message of the last failed network call on net (never NULL); net == NULL:
+ * the last failure of afqmc_net_create on this thread. */
+const char* afqmc_net_last_error(const afqmc_net* net);
+
 /* Sizes of the handle: N (physical sites 2 Nc), M, Nc. */
 afqmc_status afqmc_dims(const afqmc_handle* h, int32_t* N, int32_t* M, int32_t* Nc);
 

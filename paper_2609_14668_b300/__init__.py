@@ -32,6 +32,11 @@ class afqmc_params(ctypes.Structure):
                 ("seed", ctypes.c_uint64)]
 
 
+class afqmc_block_stats(ctypes.Structure):
+    _fields_ = [("proposed", ctypes.c_uint64), ("accepted", ctypes.c_uint64), ("flipped", ctypes.c_uint64),
+                ("max_stab_drift", ctypes.c_double)]
+
+
 class afqmc_sweep_stats(ctypes.Structure):
     _fields_ = [("proposed", ctypes.c_uint64), ("accepted", ctypes.c_uint64), ("max_stab_drift", ctypes.c_double),
                 ("launches", ctypes.c_uint64)]
@@ -57,6 +62,7 @@ class afqmc_obs(ctypes.Structure):
 _H = ctypes.c_void_p
 _P = ctypes.POINTER
 _DP = _P(ctypes.c_double)
+_FP = _P(ctypes.c_float)
 _I8P = _P(ctypes.c_int8)
 
 _SIGS = {
@@ -83,6 +89,20 @@ _SIGS = {
     "afqmc_batch_autotune": ([_P(afqmc_params), ctypes.c_int32, _P(ctypes.c_int32), ctypes.c_int32,
                               _P(ctypes.c_int32), ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_int32),
                               _P(ctypes.c_int32), _DP]),
+    "afqmc_net_create": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                          ctypes.c_uint64, ctypes.c_int32, _P(_H)]),
+    "afqmc_net_destroy": ([_H]),
+    "afqmc_net_dims": ([_H, _P(ctypes.c_int32)]),
+    "afqmc_net_get_params": ([_H, _FP]),
+    "afqmc_net_set_params": ([_H, _FP]),
+    "afqmc_net_forward": ([_H, _FP, ctypes.c_int32, _FP]),
+    "afqmc_net_inputs": ([_H, _I8P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                          _P(ctypes.c_int32), ctypes.c_int32, _FP, _FP]),
+    "afqmc_net_gradient": ([_H, _FP, _FP, ctypes.c_int32, _FP, _DP]),
+    "afqmc_net_train": ([_H, _I8P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                         ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, _DP]),
+    "afqmc_block_sweep": ([_H, _H, _P(afqmc_block_stats)]),
+    "afqmc_force_slice": ([_H, ctypes.c_int32, _I8P, _DP, _DP]),
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -95,7 +115,11 @@ _lib.afqmc_batch_last_error.restype = ctypes.c_char_p
 _lib.afqmc_batch_chain.argtypes = [_H, ctypes.c_int32]
 _lib.afqmc_batch_chain.restype = _H
 
-EXPORTED = sorted(list(_SIGS) + ["afqmc_last_error", "afqmc_batch_last_error", "afqmc_batch_chain"])
+_lib.afqmc_net_last_error.argtypes = [_H]
+_lib.afqmc_net_last_error.restype = ctypes.c_char_p
+
+EXPORTED = sorted(list(_SIGS) + ["afqmc_last_error", "afqmc_batch_last_error", "afqmc_batch_chain",
+                                 "afqmc_net_last_error"])
 
 
 class AfqmcError(RuntimeError):
@@ -301,6 +325,132 @@ def afqmc_batch_autotune(params_list, n_delays, ctas, n_timed=1):
 def afqmc_batch_last_error(b=None):
     m = _lib.afqmc_batch_last_error(b)
     return m.decode() if m else ""
+
+
+def _check_net(code, net):
+    if code != 0:
+        msg = _lib.afqmc_net_last_error(net)
+        raise AfqmcError(code, msg.decode() if msg else "")
+
+
+def _fptr(a):
+    return a.ctypes.data_as(_FP)
+
+
+def afqmc_net_create(b, T, h, ht, hidden, seed=0, device=0):
+    net = _H()
+    _check_net(_lib.afqmc_net_create(b, T, h, ht, hidden, seed, device, ctypes.byref(net)), None)
+    return net
+
+
+def afqmc_net_destroy(net):
+    _lib.afqmc_net_destroy(net)
+
+
+def afqmc_net_dims(net):
+    d = (ctypes.c_int32 * 4)()
+    _check_net(_lib.afqmc_net_dims(net, d), net)
+    return tuple(d)
+
+
+def afqmc_net_get_params(net):
+    p = np.empty(afqmc_net_dims(net)[3], dtype=np.float32)
+    _check_net(_lib.afqmc_net_get_params(net, _fptr(p)), net)
+    return p
+
+
+def afqmc_net_set_params(net, p):
+    p = np.ascontiguousarray(p, dtype=np.float32)
+    _check_net(_lib.afqmc_net_set_params(net, _fptr(p)), net)
+
+
+def afqmc_net_forward(net, X):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    d_in, _, d_out, _ = afqmc_net_dims(net)
+    Z = np.empty((X.shape[0], d_out), dtype=np.float32)
+    _check_net(_lib.afqmc_net_forward(net, _fptr(X), X.shape[0], _fptr(Z)), net)
+    return Z
+
+
+def afqmc_net_inputs(net, fields, L1, L2, pos):
+    f = np.ascontiguousarray(fields, dtype=np.int8)
+    p = np.ascontiguousarray(pos, dtype=np.int32).reshape(-1, 4)
+    d_in, _, d_out, _ = afqmc_net_dims(net)
+    X = np.empty((p.shape[0], d_in), dtype=np.float32)
+    S = np.empty((p.shape[0], d_out), dtype=np.float32)
+    _check_net(_lib.afqmc_net_inputs(net, f.ctypes.data_as(_I8P), f.shape[0], L1, L2, f.shape[1],
+                                     p.ctypes.data_as(_P(ctypes.c_int32)), p.shape[0], _fptr(X), _fptr(S)), net)
+    return X, S
+
+
+def afqmc_net_gradient(net, X, S):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    S = np.ascontiguousarray(S, dtype=np.float32)
+    g = np.empty(afqmc_net_dims(net)[3], dtype=np.float32)
+    loss = ctypes.c_double()
+    _check_net(_lib.afqmc_net_gradient(net, _fptr(X), _fptr(S), X.shape[0], _fptr(g), ctypes.byref(loss)), net)
+    return g, loss.value
+
+
+def afqmc_net_train(net, fields, L1, L2, n_steps, batch, lr=1e-3, seed=0):
+    f = np.ascontiguousarray(fields, dtype=np.int8)
+    loss = ctypes.c_double()
+    _check_net(_lib.afqmc_net_train(net, f.ctypes.data_as(_I8P), f.shape[0], L1, L2, f.shape[1], n_steps, batch,
+                                    lr, seed, ctypes.byref(loss)), net)
+    return loss.value
+
+
+def afqmc_net_last_error(net=None):
+    m = _lib.afqmc_net_last_error(net)
+    return m.decode() if m else ""
+
+
+def afqmc_block_sweep(h, net):
+    st = afqmc_block_stats()
+    _check(_lib.afqmc_block_sweep(h, net, ctypes.byref(st)), h)
+    return st
+
+
+def afqmc_force_slice(h, slice_, mask, G):
+    B = np.array(G, dtype=_gdtype(h), order="C", copy=True)
+    m = np.ascontiguousarray(mask, dtype=np.int8)
+    lr = ctypes.c_double()
+    _check(_lib.afqmc_force_slice(h, slice_, m.ctypes.data_as(_I8P), _dptr(B), ctypes.byref(lr)), h)
+    return B, lr.value
+
+
+class Net:
+    """Block-proposal network (owns an afqmc_net)."""
+
+    def __init__(self, b, T, h, ht, hidden, seed=0, device=0):
+        self.shape = (b, T, h, ht, hidden)
+        self.net = afqmc_net_create(b, T, h, ht, hidden, seed, device)
+        self.d_in, self.d_hid, self.d_out, self.n_params = afqmc_net_dims(self.net)
+
+    def params(self):
+        """Split parameter vector: W1, b1, W2, b2."""
+        p = afqmc_net_get_params(self.net)
+        a = self.d_hid * self.d_in
+        W1 = p[:a].reshape(self.d_hid, self.d_in)
+        b1 = p[a:a + self.d_hid]
+        c = a + self.d_hid
+        W2 = p[c:c + self.d_out * self.d_hid].reshape(self.d_out, self.d_hid)
+        b2 = p[c + self.d_out * self.d_hid:]
+        return dict(W1=W1, b1=b1, W2=W2, b2=b2)
+
+    def set_params(self, d):
+        afqmc_net_set_params(self.net, np.concatenate([np.ravel(d[k]) for k in ("W1", "b1", "W2", "b2")]))
+
+    def close(self):
+        if self.net:
+            afqmc_net_destroy(self.net)
+            self.net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def afqmc_last_error(h=None):

@@ -10,12 +10,14 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <random>
 #include <mutex>
 #include <string>
 #include <vector>
 
 #include "afqmc.h"
 #include "common.cuh"
+#include "learned.cuh"
 #include "linalg.cuh"
 #include "measure.cuh"
 #include "update.cuh"
@@ -88,6 +90,16 @@ struct afqmc_handle {
     double *czz = nullptr, *hab = nullptr;                     // per-measurement scratch
     double *obs_now = nullptr, *czz_now = nullptr, *nk_now = nullptr;
     double *obs_acc = nullptr, *czz_acc = nullptr, *nk_acc = nullptr;
+    // block moves (allocated on the first block pass)
+    double* Gsave = nullptr;
+    int8_t *fsave = nullptr, *bmask = nullptr;
+    double *logR = nullptr, *lq = nullptr;
+    int* bflag = nullptr;
+    unsigned long long* bstats = nullptr;
+    float *bX = nullptr, *bH = nullptr, *bZ = nullptr;
+    int* bpos = nullptr;
+    size_t bcap_in = 0, bcap_hid = 0, bcap_out = 0, bcap_T = 0;
+    uint64_t block_passes = 0;
     long long* obs_count = nullptr;
     std::vector<UDTe> Rst, Lst;
     UDTe tmpA, tmpB;               // scratch entries for get_G
@@ -374,13 +386,15 @@ void half_step(afqmc_handle* h, const double* A, double* out) {
 
 // sweep < 0: the sweep number is the device-resident one (sweep path, graph
 // replays); otherwise the given number (test hooks).
-void update_slice(afqmc_handle* h, double* G, int l, int pass, int64_t sweep) {
+void update_slice(afqmc_handle* h, double* G, int l, int pass, int64_t sweep, const int8_t* force = nullptr,
+                  double* logR = nullptr) {
     UpdArgs a{};
     a.G = G; a.N = h->N; a.Xs = h->Xs; a.Ys = h->Ys; a.msite = h->msite; a.mcoef = h->mcoef;
     a.xw = h->xw; a.yw = h->yw; a.Gw = h->Gw; a.ctl = h->ctl;
     a.s = h->field + (size_t)(l - 1) * h->Np;
     a.nd = h->nd; a.W = h->W;
     a.pair = h->cplx; a.Np = h->Np;
+    a.force = force; a.logR = logR; a.two_gamma = 2.0 * h->gamma;
     a.dl_p = h->dl_p; a.dl_m = h->dl_m; a.ef_p = h->ef_p; a.ef_m = h->ef_m;
     a.key = h->key;
     a.ctr_stride = 2ull * (uint64_t)h->M * (uint64_t)h->Np;
@@ -1215,6 +1229,405 @@ afqmc_status afqmc_batch_autotune(const afqmc_params* params, int32_t n, const i
 
 const char* afqmc_batch_last_error(const afqmc_batch* b) {
     return b ? b->err.c_str() : g_batch_error.c_str();
+}
+
+}  // extern "C"
+
+// ====================================================================== learned block proposals
+struct afqmc_net {
+    int device = 0;
+    int b = 0, T = 0, h = 0, ht = 0, W = 0;
+    int d_in = 0, d_hid = 0, d_out = 0, n_par = 0;
+    float *P = nullptr, *m = nullptr, *v = nullptr, *G = nullptr;
+    int step = 0;
+    cudaStream_t stream = nullptr;
+    // training scratch (grown on demand)
+    float *X = nullptr, *S = nullptr, *Hd = nullptr, *Z = nullptr, *dZ = nullptr, *dA = nullptr;
+    int* pos = nullptr;
+    double* loss = nullptr;
+    int cap_B = 0;
+    int8_t* fields = nullptr;
+    size_t cap_fields = 0;
+    std::string err;
+    std::vector<void*> allocs;
+    template <class T_>
+    T_* dalloc(size_t n) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaMalloc(&ptr, n * sizeof(T_) > 0 ? n * sizeof(T_) : 16);
+        if (e != cudaSuccess) throw CudaFail{AFQMC_E_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+        allocs.push_back(ptr);
+        return static_cast<T_*>(ptr);
+    }
+    void dfree(void* ptr) {
+        for (auto& a : allocs) if (a == ptr) { cudaFree(a); a = nullptr; }
+    }
+};
+
+namespace {
+
+thread_local std::string g_net_error;
+
+BlockGeom geom_of(const afqmc_net* n, int L1, int L2, int M) {
+    BlockGeom g{};
+    g.L1 = L1; g.L2 = L2; g.Nc = L1 * L2; g.Np = 2 * L1 * L2; g.M = M;
+    g.b = n->b; g.T = n->T; g.h = n->h; g.ht = n->ht; g.W = n->W;
+    g.d_in = n->d_in; g.d_out = n->d_out; g.d_hid = n->d_hid;
+    return g;
+}
+
+void net_reserve(afqmc_net* n, int B) {
+    if (B <= n->cap_B) return;
+    for (void* ptr : {(void*)n->X, (void*)n->S, (void*)n->Hd, (void*)n->Z, (void*)n->dZ, (void*)n->dA, (void*)n->pos})
+        if (ptr) n->dfree(ptr);
+    n->X = n->dalloc<float>((size_t)B * n->d_in);
+    n->S = n->dalloc<float>((size_t)B * n->d_out);
+    n->Hd = n->dalloc<float>((size_t)B * n->d_hid);
+    n->Z = n->dalloc<float>((size_t)B * n->d_out);
+    n->dZ = n->dalloc<float>((size_t)B * n->d_out);
+    n->dA = n->dalloc<float>((size_t)B * n->d_hid);
+    n->pos = n->dalloc<int>((size_t)4 * B);
+    n->cap_B = B;
+}
+
+unsigned grid_of(size_t work, int threads = 256) { return (unsigned)((work + threads - 1) / threads); }
+
+// Z = net(X) for B contexts already on the device (stream s)
+void net_forward_dev(afqmc_net* n, const float* X, int B, float* Hd, float* Z, cudaStream_t s) {
+    k_mlp_hidden<<<grid_of((size_t)B * n->d_hid), 256, 0, s>>>(n->P, X, B, n->d_in, n->d_hid, Hd);
+    k_mlp_out<<<grid_of((size_t)B * n->d_out), 256, 0, s>>>(n->P, Hd, B, n->d_in, n->d_hid, n->d_out, Z);
+    CK(cudaGetLastError());
+}
+
+// gradient of the mean loss into n->G, loss added to n->loss (n->X, n->S hold the batch)
+void net_gradient_dev(afqmc_net* n, int B) {
+    cudaStream_t s = n->stream;
+    net_forward_dev(n, n->X, B, n->Hd, n->Z, s);
+    k_mlp_dz<<<std::min(grid_of((size_t)B * n->d_out), 1024u), 256, 0, s>>>(n->Z, n->S, B, n->d_out, n->dZ, n->loss);
+    k_mlp_grad_out<<<grid_of((size_t)n->d_out * n->d_hid + n->d_out), 256, 0, s>>>(n->dZ, n->Hd, B, n->d_in, n->d_hid,
+                                                                                  n->d_out, n->G);
+    k_mlp_dA<<<grid_of((size_t)B * n->d_hid), 256, 0, s>>>(n->P, n->dZ, n->Hd, B, n->d_in, n->d_hid, n->d_out, n->dA);
+    k_mlp_grad_hidden<<<grid_of((size_t)n->d_hid * n->d_in + n->d_hid), 256, 0, s>>>(n->dA, n->X, B, n->d_in,
+                                                                                     n->d_hid, n->G);
+    CK(cudaGetLastError());
+}
+
+// Per-handle buffers of the block pass, sized for this network.
+void block_reserve(afqmc_handle* h, const afqmc_net* n) {
+    if (!h->Gsave) {
+        h->Gsave = h->dalloc<double>((size_t)h->N * h->N);
+        h->logR = h->dalloc<double>(1);
+        h->lq = h->dalloc<double>(2);
+        h->bflag = h->dalloc<int>(1);
+        h->bstats = h->dalloc<unsigned long long>(3);
+        h->bpos = h->dalloc<int>(4);
+    }
+    if ((size_t)n->T > h->bcap_T) {
+        h->fsave = h->dalloc<int8_t>((size_t)n->T * h->Np);
+        h->bmask = h->dalloc<int8_t>((size_t)n->T * h->Np);
+        h->bcap_T = n->T;
+    }
+    if ((size_t)n->d_in > h->bcap_in) { h->bX = h->dalloc<float>(n->d_in); h->bcap_in = n->d_in; }
+    if ((size_t)n->d_hid > h->bcap_hid) { h->bH = h->dalloc<float>(n->d_hid); h->bcap_hid = n->d_hid; }
+    if ((size_t)n->d_out > h->bcap_out) { h->bZ = h->dalloc<float>(n->d_out); h->bcap_out = n->d_out; }
+}
+
+// One block move at window l0, offset (o1, o2); G enters and leaves at slice l0 - 1.
+void block_move(afqmc_handle* h, afqmc_net* n, const BlockGeom& g, int l0, int o1, int o2, uint64_t ctr) {
+    const size_t nn = (size_t)h->N * h->N, nf = (size_t)n->T * h->Np;
+    int8_t* fwin = h->field + (size_t)(l0 - 1) * h->Np;
+    CK(cudaMemcpyAsync(h->Gsave, h->G, sizeof(double) * nn, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->fsave, fwin, nf, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemsetAsync(h->bmask, 0, nf, h->stream));
+    CK(cudaMemsetAsync(h->logR, 0, sizeof(double), h->stream));
+    const int pos[4] = {0, l0, o1, o2};
+    CK(cudaMemcpyAsync(h->bpos, pos, sizeof(pos), cudaMemcpyHostToDevice, h->stream));
+    {
+        Scope sc(h, AFQMC_K_MISC);
+        k_block_inputs<<<1, 256, 0, h->stream>>>(h->field, 0, h->bpos, g, h->bX, nullptr);
+        net_forward_dev(n, h->bX, 1, h->bH, h->bZ, h->stream);
+        k_block_propose<<<1, 256, 0, h->stream>>>(h->bZ, h->field, g, l0, o1, o2, h->key, ctr, h->bmask, h->lq);
+    }
+    CK(cudaGetLastError());
+    h->launches += 3;                                   // inputs + two network layers + proposal in one scope
+    h->cat_launches[AFQMC_K_MISC] += 3;
+    for (int t = 0; t < n->T; ++t) {
+        wrap(h, h->G, l0 + t, +1);
+        update_slice(h, h->G, l0 + t, 0, 0, h->bmask + (size_t)t * h->Np, h->logR);
+    }
+    { Scope sc(h, AFQMC_K_MISC);
+      k_block_accept<<<1, 256, 0, h->stream>>>(h->logR, h->lq, h->bmask, (int)nf, h->key, ctr + n->d_out, h->bflag,
+                                                h->bstats, h->st); }
+    CK(cudaGetLastError());
+    for (int t = n->T - 1; t >= 0; --t) wrap(h, h->G, l0 + t, -1);
+    { Scope sc(h, AFQMC_K_MISC);
+      k_block_restore<<<h->sms * 2, 256, 0, h->stream>>>(h->bflag, h->Gsave, h->G, nn, h->fsave, fwin, nf); }
+    CK(cudaGetLastError());
+}
+
+void block_pass(afqmc_handle* h, afqmc_net* n) {
+    const BlockGeom g = geom_of(n, h->L1, h->L2, h->M);
+    const int nwin = h->M / n->T, np1 = h->L1 / n->b, np2 = h->L2 / n->b;
+    const uint64_t base = (3ull << 62) + h->block_passes * (uint64_t)nwin * np1 * np2 * (uint64_t)(n->d_out + 1);
+    for (int w = 0; w < nwin; ++w) {
+        const int l0 = w * n->T + 1;
+        for (int p2 = 0; p2 < np2; ++p2)
+            for (int p1 = 0; p1 < np1; ++p1) {
+                const uint64_t ctr = base + ((uint64_t)(w * np2 + p2) * np1 + p1) * (uint64_t)(n->d_out + 1);
+                block_move(h, n, g, l0, p1 * n->b, p2 * n->b, ctr);
+            }
+        for (int t = 0; t < n->T; ++t) wrap(h, h->G, l0 + t, +1);
+        const int lend = l0 + n->T - 1;
+        if (lend % h->ns == 0) {
+            const int c = lend / h->ns;
+            udt_extend(h, h->Rst[c - 1], h->Rst[c], (c - 1) * h->ns + 1, c * h->ns, true);
+            recompute(h, c);
+        }
+    }
+    // the fields changed: rebuild the L stacks and G at slice 0
+    init_chain(h);
+    h->block_passes += 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+afqmc_status afqmc_net_create(int32_t b, int32_t T, int32_t hc, int32_t ht, int32_t hidden, uint64_t seed,
+                              int32_t device, afqmc_net** out) {
+    if (out) *out = nullptr;
+    if (!out || b < 1 || T < 1 || hc < 0 || ht < 0 || hidden < 1 || hidden > 4096) {
+        g_net_error = "bad network shape";
+        return AFQMC_E_INVALID;
+    }
+    auto* n = new afqmc_net();
+    try {
+        n->device = device;
+        n->b = b; n->T = T; n->h = hc; n->ht = ht; n->W = b + 2 * hc;
+        n->d_in = (T + 2 * ht) * n->W * n->W * 2;
+        n->d_hid = hidden;
+        n->d_out = T * b * b * 2;
+        n->n_par = n->d_hid * n->d_in + n->d_hid + n->d_out * n->d_hid + n->d_out;
+        CK(cudaSetDevice(device));
+        CK(cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking));
+        n->P = n->dalloc<float>(n->n_par);
+        n->m = n->dalloc<float>(n->n_par);
+        n->v = n->dalloc<float>(n->n_par);
+        n->G = n->dalloc<float>(n->n_par);
+        n->loss = n->dalloc<double>(1);
+        // W1 ~ N(0, 1/Din), W2 ~ N(0, 0.01/H), biases 0 (seeded host generator)
+        std::mt19937_64 gen(seed);
+        std::normal_distribution<float> nd(0.0f, 1.0f);
+        std::vector<float> p(n->n_par, 0.0f);
+        const float s1 = 1.0f / std::sqrt((float)n->d_in), s2 = 0.1f / std::sqrt((float)n->d_hid);
+        for (int o = 0; o < n->d_hid * n->d_in; ++o) p[o] = nd(gen) * s1;
+        const int w2 = n->d_hid * n->d_in + n->d_hid;
+        for (int o = 0; o < n->d_out * n->d_hid; ++o) p[w2 + o] = nd(gen) * s2;
+        CK(cudaMemcpy(n->P, p.data(), sizeof(float) * n->n_par, cudaMemcpyHostToDevice));
+        CK(cudaMemset(n->m, 0, sizeof(float) * n->n_par));
+        CK(cudaMemset(n->v, 0, sizeof(float) * n->n_par));
+    } catch (const CudaFail& f) {
+        g_net_error = f.msg;
+        afqmc_net_destroy(n);
+        return f.code;
+    }
+    *out = n;
+    return AFQMC_OK;
+}
+
+afqmc_status afqmc_net_destroy(afqmc_net* n) {
+    if (!n) return AFQMC_OK;
+    if (n->stream) cudaStreamSynchronize(n->stream);
+    for (void* ptr : n->allocs) if (ptr) cudaFree(ptr);
+    if (n->stream) cudaStreamDestroy(n->stream);
+    delete n;
+    return AFQMC_OK;
+}
+
+afqmc_status afqmc_net_dims(const afqmc_net* n, int32_t dims[4]) {
+    if (!n || !dims) return AFQMC_E_INVALID;
+    dims[0] = n->d_in; dims[1] = n->d_hid; dims[2] = n->d_out; dims[3] = n->n_par;
+    return AFQMC_OK;
+}
+
+#define NET_BEGIN(n)   if (!(n)) return AFQMC_E_INVALID; try {
+#define NET_END(n)     } catch (const CudaFail& f) { (n)->err = f.msg; return f.code; }
+
+afqmc_status afqmc_net_get_params(afqmc_net* n, float* host) {
+    NET_BEGIN(n)
+    if (!host) { n->err = "null output"; return AFQMC_E_INVALID; }
+    CK(cudaMemcpyAsync(host, n->P, sizeof(float) * n->n_par, cudaMemcpyDeviceToHost, n->stream));
+    CK(cudaStreamSynchronize(n->stream));
+    return AFQMC_OK;
+    NET_END(n)
+}
+
+afqmc_status afqmc_net_set_params(afqmc_net* n, const float* host) {
+    NET_BEGIN(n)
+    if (!host) { n->err = "null input"; return AFQMC_E_INVALID; }
+    CK(cudaMemcpyAsync(n->P, host, sizeof(float) * n->n_par, cudaMemcpyHostToDevice, n->stream));
+    CK(cudaMemsetAsync(n->m, 0, sizeof(float) * n->n_par, n->stream));
+    CK(cudaMemsetAsync(n->v, 0, sizeof(float) * n->n_par, n->stream));
+    n->step = 0;
+    CK(cudaStreamSynchronize(n->stream));
+    return AFQMC_OK;
+    NET_END(n)
+}
+
+afqmc_status afqmc_net_inputs(afqmc_net* n, const int8_t* fields, int32_t n_cfg, int32_t L1, int32_t L2, int32_t M,
+                              const int32_t* pos, int32_t B, float* X, float* S) {
+    NET_BEGIN(n)
+    if (!fields || !pos || !X || n_cfg < 1 || L1 < 1 || L2 < 1 || M < 1 || B < 1) { n->err = "bad arguments"; return AFQMC_E_INVALID; }
+    for (int q = 0; q < B; ++q)
+        if (pos[4 * q] < 0 || pos[4 * q] >= n_cfg || pos[4 * q + 1] < 1 || pos[4 * q + 1] + n->T - 1 > M) {
+            n->err = "block position outside the configurations";
+            return AFQMC_E_INVALID;
+        }
+    const size_t stride = (size_t)M * 2 * L1 * L2;
+    net_reserve(n, B);
+    int8_t* f = n->dalloc<int8_t>((size_t)n_cfg * stride);
+    CK(cudaMemcpyAsync(f, fields, (size_t)n_cfg * stride, cudaMemcpyHostToDevice, n->stream));
+    CK(cudaMemcpyAsync(n->pos, pos, sizeof(int) * 4 * B, cudaMemcpyHostToDevice, n->stream));
+    k_block_inputs<<<B, 256, 0, n->stream>>>(f, stride, n->pos, geom_of(n, L1, L2, M), n->X, S ? n->S : nullptr);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(X, n->X, sizeof(float) * B * n->d_in, cudaMemcpyDeviceToHost, n->stream));
+    if (S) CK(cudaMemcpyAsync(S, n->S, sizeof(float) * B * n->d_out, cudaMemcpyDeviceToHost, n->stream));
+    CK(cudaStreamSynchronize(n->stream));
+    n->dfree(f);
+    return AFQMC_OK;
+    NET_END(n)
+}
+
+afqmc_status afqmc_net_forward(afqmc_net* n, const float* X, int32_t B, float* Z) {
+    NET_BEGIN(n)
+    if (!X || !Z || B < 1) { n->err = "bad arguments"; return AFQMC_E_INVALID; }
+    net_reserve(n, B);
+    CK(cudaMemcpyAsync(n->X, X, sizeof(float) * B * n->d_in, cudaMemcpyHostToDevice, n->stream));
+    net_forward_dev(n, n->X, B, n->Hd, n->Z, n->stream);
+    CK(cudaMemcpyAsync(Z, n->Z, sizeof(float) * B * n->d_out, cudaMemcpyDeviceToHost, n->stream));
+    CK(cudaStreamSynchronize(n->stream));
+    return AFQMC_OK;
+    NET_END(n)
+}
+
+afqmc_status afqmc_net_gradient(afqmc_net* n, const float* X, const float* S, int32_t B, float* grad, double* loss) {
+    NET_BEGIN(n)
+    if (!X || !S || !grad || B < 1) { n->err = "bad arguments"; return AFQMC_E_INVALID; }
+    net_reserve(n, B);
+    CK(cudaMemcpyAsync(n->X, X, sizeof(float) * B * n->d_in, cudaMemcpyHostToDevice, n->stream));
+    CK(cudaMemcpyAsync(n->S, S, sizeof(float) * B * n->d_out, cudaMemcpyHostToDevice, n->stream));
+    CK(cudaMemsetAsync(n->loss, 0, sizeof(double), n->stream));
+    net_gradient_dev(n, B);
+    CK(cudaMemcpyAsync(grad, n->G, sizeof(float) * n->n_par, cudaMemcpyDeviceToHost, n->stream));
+    double l = 0.0;
+    CK(cudaMemcpyAsync(&l, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
+    CK(cudaStreamSynchronize(n->stream));
+    if (loss) *loss = l;
+    return AFQMC_OK;
+    NET_END(n)
+}
+
+afqmc_status afqmc_net_train(afqmc_net* n, const int8_t* fields, int32_t n_cfg, int32_t L1, int32_t L2, int32_t M,
+                             int32_t n_steps, int32_t batch, float lr, uint64_t seed, double* loss) {
+    NET_BEGIN(n)
+    if (!fields || n_cfg < 1 || L1 < 1 || L2 < 1 || M < n->T || n_steps < 0 || batch < 1 || batch > 65536 ||
+        L1 % n->b || L2 % n->b) {
+        n->err = "bad training arguments (sizes, or b must divide L1 and L2, T <= M)";
+        return AFQMC_E_INVALID;
+    }
+    const size_t stride = (size_t)M * 2 * L1 * L2;
+    if ((size_t)n_cfg * stride > n->cap_fields) {
+        if (n->fields) n->dfree(n->fields);
+        n->fields = n->dalloc<int8_t>((size_t)n_cfg * stride);
+        n->cap_fields = (size_t)n_cfg * stride;
+    }
+    CK(cudaMemcpyAsync(n->fields, fields, (size_t)n_cfg * stride, cudaMemcpyHostToDevice, n->stream));
+    net_reserve(n, batch);
+    const BlockGeom g = geom_of(n, L1, L2, M);
+    std::mt19937_64 gen(seed);
+    std::vector<int> pos((size_t)4 * batch);
+    double l = 0.0;
+    for (int it = 0; it < n_steps; ++it) {
+        for (int q = 0; q < batch; ++q) {
+            pos[4 * q] = (int)(gen() % (uint64_t)n_cfg);
+            pos[4 * q + 1] = 1 + (int)(gen() % (uint64_t)(M - n->T + 1));
+            pos[4 * q + 2] = (int)(gen() % (uint64_t)L1);
+            pos[4 * q + 3] = (int)(gen() % (uint64_t)L2);
+        }
+        CK(cudaMemcpyAsync(n->pos, pos.data(), sizeof(int) * 4 * batch, cudaMemcpyHostToDevice, n->stream));
+        CK(cudaStreamSynchronize(n->stream));     // pos is reused by the next step
+        CK(cudaMemsetAsync(n->loss, 0, sizeof(double), n->stream));
+        k_block_inputs<<<batch, 256, 0, n->stream>>>(n->fields, stride, n->pos, g, n->X, n->S);
+        CK(cudaGetLastError());
+        net_gradient_dev(n, batch);
+        n->step += 1;
+        const float bc1 = 1.0f - std::pow(0.9f, (float)n->step), bc2 = 1.0f - std::pow(0.999f, (float)n->step);
+        k_adam<<<grid_of(n->n_par), 256, 0, n->stream>>>(n->P, n->G, n->m, n->v, n->n_par, lr, bc1, bc2);
+        CK(cudaGetLastError());
+    }
+    if (n_steps > 0) CK(cudaMemcpyAsync(&l, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
+    CK(cudaStreamSynchronize(n->stream));
+    if (loss) *loss = l;
+    return AFQMC_OK;
+    NET_END(n)
+}
+
+const char* afqmc_net_last_error(const afqmc_net* n) { return n ? n->err.c_str() : g_net_error.c_str(); }
+
+afqmc_status afqmc_block_sweep(afqmc_handle* h, afqmc_net* n, afqmc_block_stats* stats) {
+    API_BEGIN(h)
+    if (!n) { h->err = "null network"; return AFQMC_E_INVALID; }
+    if (h->cplx) { h->err = "block moves need a periodic (real) chain"; return AFQMC_E_INVALID; }
+    if (h->ns % n->T || h->L1 % n->b || h->L2 % n->b || n->device != h->p.device) {
+        h->err = "block shape does not fit the chain (T | n_stab, b | L1, b | L2, same device)";
+        return AFQMC_E_INVALID;
+    }
+    block_reserve(h, n);
+    CK(cudaStreamSynchronize(n->stream));       // parameters written on the network's stream
+    CK(cudaMemsetAsync(h->bstats, 0, sizeof(unsigned long long) * 3, h->stream));
+    CK(cudaMemsetAsync(h->drift, 0, sizeof(unsigned long long), h->stream));
+    block_pass(h, n);
+    unsigned long long bs[3] = {0, 0, 0}, dr = 0;
+    CK(cudaMemcpyAsync(bs, h->bstats, sizeof(bs), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&dr, h->drift, sizeof(dr), cudaMemcpyDeviceToHost, h->stream));
+    afqmc_status s = check_device(h);
+    if (stats) {
+        stats->proposed = bs[0];
+        stats->accepted = bs[1];
+        stats->flipped = bs[2];
+        std::memcpy(&stats->max_stab_drift, &dr, sizeof(double));
+    }
+    return s;
+    API_END(h)
+}
+
+afqmc_status afqmc_force_slice(afqmc_handle* h, int32_t slice, const int8_t* mask, double* G, double* logR) {
+    API_BEGIN(h)
+    if (!mask || !G || slice < 1 || slice > h->M) { h->err = "bad arguments"; return AFQMC_E_INVALID; }
+    if (!h->Gsave) {
+        h->Gsave = h->dalloc<double>((size_t)h->N * h->N);
+        h->logR = h->dalloc<double>(1);
+        h->lq = h->dalloc<double>(2);
+        h->bflag = h->dalloc<int>(1);
+        h->bstats = h->dalloc<unsigned long long>(3);
+        h->bpos = h->dalloc<int>(4);
+    }
+    if (!h->bmask || h->bcap_T < 1) {
+        h->bmask = h->dalloc<int8_t>(h->Np);
+        h->fsave = h->dalloc<int8_t>(h->Np);
+        h->bcap_T = 1;
+    }
+    double* d = h->Wk[5];
+    from_host(h, G, d, h->Wk[4]);
+    CK(cudaMemcpyAsync(h->bmask, mask, h->Np, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(h->logR, 0, sizeof(double), h->stream));
+    update_slice(h, d, slice, 0, 0, h->bmask, h->logR);
+    to_host(h, d, G, h->Wk[4]);
+    double lr = 0.0;
+    CK(cudaMemcpyAsync(&lr, h->logR, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    afqmc_status s = check_device(h);
+    if (logR) *logR = lr;
+    return s;
+    API_END(h)
 }
 
 afqmc_status afqmc_dims(const afqmc_handle* h, int32_t* N, int32_t* M, int32_t* Nc) {

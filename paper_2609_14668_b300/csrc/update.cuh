@@ -48,6 +48,11 @@ struct UpdArgs {
     int precision;                // 0: FP64 flush; 1: split-TF32 tcgen05 flush, FP32 accumulate
     int pair;                     // 1: G is the real 2Np x 2Np embedding of a complex G (twist)
     int Np;                       // physical sites (field length); N = 2 Np when pair
+    // forced mode (block moves): flip exactly the sites with force[i] != 0, no
+    // random test, and add log R = 2 gamma s + log |r|^2 of every flip to *logR
+    const int8_t* force;
+    double* logR;
+    double two_gamma;
 };
 
 // Window of the proposals.  Plain: positions t = 0..nw-1 are the sites c0 + t.
@@ -297,15 +302,21 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
             for (int t = threadIdx.x; t < nw; t += blockDim.x) {
                 const int ps = win_phys(a, cursor, t);
                 const int sg = a.s[ps];
-                const double u = sm64_uniform(a.key, ctr0 + ps);
-                // accept iff u < e^{2 gamma s} r^2  <=>  r^2 > u e^{-2 gamma s}
-                vv[t] = u * (sg > 0 ? a.ef_m : a.ef_p);
+                if (a.force) {
+                    // forced: threshold -1 accepts any real r, +inf accepts none
+                    vv[t] = a.force[ps] ? -1.0 : __longlong_as_double(0x7ff0000000000000ll);
+                } else {
+                    const double u = sm64_uniform(a.key, ctr0 + ps);
+                    // accept iff u < e^{2 gamma s} r^2  <=>  r^2 > u e^{-2 gamma s}
+                    vv[t] = u * (sg > 0 ? a.ef_m : a.ef_p);
+                }
                 dd[t] = sg > 0 ? a.dl_p : a.dl_m;
                 od[t] = 1.0 + dd[t];
                 sw[t] = (int8_t)sg;
             }
             __syncthreads();
             int kk = k, tstop = nw, t0 = 0, it = 0;
+            double lacc = 0.0;                            // forced mode: sum of log R (thread 0)
             for (;; ++it) {
                 const int slot = it & 1;
                 if (threadIdx.x == 0) {
@@ -331,6 +342,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                             if (r * r2 > vv[t0]) {
                                 found = t0;
                                 c = c1;
+                                if (a.force) lacc += log(r * r2) + a.two_gamma * sw[t0];
                                 break;
                             }
                             ++t0;                    // rejected: skip the partner too
@@ -339,6 +351,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                         if (r * r > vv[t0]) {
                             found = t0;
                             c = dl * recip_nr(r);
+                            if (a.force) lacc += log(r * r) + a.two_gamma * sw[t0];
                             break;
                         }
                     }
@@ -386,6 +399,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                 if (kk == nd) { tstop = tf + 1; break; }
             }
             if (threadIdx.x == 0) {
+                if (a.force) *a.logR += lacc;
                 a.ctl[0] = cursor;
                 a.ctl[1] = k;
                 a.ctl[2] = kk;
