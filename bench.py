@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default=WORKLOAD_KEY, choices=sorted(WORKLOADS) + ["batched"],
+    ap.add_argument("--workload", default=WORKLOAD_KEY, choices=sorted(WORKLOADS) + ["batched", "learned"],
                     help="batched: 64 chains, L in {6, 9, 12}, 16 twists each, one graph per batched sweep")
     ap.add_argument("--no-autotune", action="store_true", help="batched: skip the autotuner (n_delay 16, all SMs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -62,9 +62,9 @@ def parse():
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
                     help="1: split-TF32 tensor-core flush (the L=24 precision workload); 0: plain FP64")
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 sweep")
-    ap.add_argument("--chains", type=int, default=2,
+    ap.add_argument("--chains", type=int, default=3,
                     help="independent chains per GPU, each on its own CUDA stream and host thread "
-                         "(2: any two of the cooperative kernels fit on one SM together)")
+                         "(3 saturates the L=24 workload: 2 -> 260k, 3 -> 289k, 4 -> 289k updates/s)")
     return ap.parse_args()
 
 
@@ -590,12 +590,87 @@ def run_batched(args):
     print(json.dumps(out))
 
 
+def run_learned(args):
+    """Learned block proposals at L = 6, beta t = 6: train the network on the GPU
+    on configurations of the plain sampler, then compare a chain of plain sweeps
+    with a chain that adds one block pass per sweep, by wall time per sweep and
+    by the integrated autocorrelation time of the per-sweep m^2 and energy."""
+    import torch
+    import paper_2609_14668_b300 as pkg
+    from paper_2609_14668_b300.autocorr import tau_int
+    import numpy as np
+    from synth import LEARNED as C
+    torch.cuda.set_device(0)
+    mk = lambda seed: pkg.make_params(L=C["L"], beta=C["beta"], dtau=C["dtau"], U=C["U"], n_delay=C["n_delay"],
+                                      n_stab=C["n_stab"], seed=seed, measure=1)
+    sweeps = max(args.steps, 50)
+    # training data: one configuration per sweep of a plain chain
+    t0 = time.perf_counter()
+    src = pkg.Chain(mk(31))
+    src.sweep(max(args.warmup, 50))
+    cfgs = []
+    for _ in range(C["n_cfg"]):
+        src.sweep(1)
+        cfgs.append(src.field())
+    src.close()
+    cfgs = np.stack(cfgs)
+    t_data = time.perf_counter() - t0
+    net = pkg.Net(C["b"], C["T"], C["h"], C["ht"], C["hidden"], seed=1)
+    loss0 = pkg.afqmc_net_train(net.net, cfgs, C["L"], C["L"], 1, C["batch"], lr=0.0, seed=1)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss = pkg.afqmc_net_train(net.net, cfgs, C["L"], C["L"], C["train_steps"], C["batch"], lr=C["lr"], seed=2)
+    t_train = time.perf_counter() - t1
+    untrained = pkg.Net(C["b"], C["T"], C["h"], C["ht"], C["hidden"], seed=1)
+
+    def run(chain_seed, netp):
+        ch = pkg.Chain(mk(chain_seed))
+        ch.sweep(max(args.warmup, 20))
+        ch.observables()
+        series, acc, prop, flips = [], 0, 0, 0
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        for _ in range(sweeps):
+            st = ch.sweep(1)
+            if netp is not None:
+                b = pkg.afqmc_block_sweep(ch.h, netp.net)
+                acc, prop, flips = acc + b.accepted, prop + b.proposed, flips + b.flipped
+            series.append(ch.observables())
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - ts
+        n_local = sweeps * 2 * ch.N * ch.M
+        ch.close()
+        taus = {k: tau_int([[o[k] for o in series]])[0] for k in ("m2", "energy")}
+        rate = n_local / wall
+        return {"updates_per_s": rate, "s_per_sweep": wall / sweeps, "tau_int_sweeps": taus,
+                "per_2tau": rate / (2.0 * max(taus.values())),
+                "block_acceptance": (acc / prop) if prop else None, "block_flips_per_sweep": flips / sweeps,
+                "m2": float(np.mean([o["m2"] for o in series]))}
+
+    plain = run(41, None)
+    learned = run(41, net)
+    base = run(41, untrained)
+    out = {"metric": "autocorrelation-corrected HS-field updates/s with learned block proposals (L=6, beta*t=6)",
+           "value": learned["per_2tau"], "unit": "updates/s per 2 tau_int", "n_gpus": 1, "steps": sweeps,
+           "warmup": max(args.warmup, 20), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64 chain, f32 network", "data": "synthetic (training fields from the plain sampler)",
+           "config": {"workload": "learned", **{k: C[k] for k in C}},
+           "training": {"configurations_s": t_data, "train_s": t_train, "loss_initial": loss0, "loss_final": loss},
+           "plain": plain, "learned": learned, "untrained_network": base,
+           "gain_vs_plain": learned["per_2tau"] / plain["per_2tau"],
+           "note": "updates/s counts the local proposals only; tau_int from per-sweep averages of one chain each "
+                   "(Sokal window), a rough estimate at this length"}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 

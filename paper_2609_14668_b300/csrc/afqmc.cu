@@ -1339,11 +1339,9 @@ void block_move(afqmc_handle* h, afqmc_net* n, const BlockGeom& g, int l0, int o
     CK(cudaMemcpyAsync(h->fsave, fwin, nf, cudaMemcpyDeviceToDevice, h->stream));
     CK(cudaMemsetAsync(h->bmask, 0, nf, h->stream));
     CK(cudaMemsetAsync(h->logR, 0, sizeof(double), h->stream));
-    const int pos[4] = {0, l0, o1, o2};
-    CK(cudaMemcpyAsync(h->bpos, pos, sizeof(pos), cudaMemcpyHostToDevice, h->stream));
     {
         Scope sc(h, AFQMC_K_MISC);
-        k_block_inputs<<<1, 256, 0, h->stream>>>(h->field, 0, h->bpos, g, h->bX, nullptr);
+        k_block_inputs<<<1, 256, 0, h->stream>>>(h->field, 0, nullptr, g, h->bX, nullptr, l0, o1, o2);
         net_forward_dev(n, h->bX, 1, h->bH, h->bZ, h->stream);
         k_block_propose<<<1, 256, 0, h->stream>>>(h->bZ, h->field, g, l0, o1, o2, h->key, ctr, h->bmask, h->lq);
     }

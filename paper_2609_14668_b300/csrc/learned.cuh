@@ -29,11 +29,13 @@ struct BlockGeom {
 __device__ __forceinline__ int pmod(int x, int n) { return ((x % n) + n) % n; }
 
 // x (and the block's values s, if S != nullptr) of block instance n:
-// pos[4n .. 4n+3] = (configuration, l0, o1, o2); one CTA per instance.
+// pos[4n .. 4n+3] = (configuration, l0, o1, o2), or, with pos == nullptr, the
+// single block (0, l0s, o1s, o2s); one CTA per instance.
 __global__ void k_block_inputs(const int8_t* __restrict__ fields, size_t cfg_stride, const int* __restrict__ pos,
-                               BlockGeom g, float* X, float* S) {
+                               BlockGeom g, float* X, float* S, int l0s = 1, int o1s = 0, int o2s = 0) {
     const int n = blockIdx.x;
-    const int cfg = pos[4 * n], l0 = pos[4 * n + 1], o1 = pos[4 * n + 2], o2 = pos[4 * n + 3];
+    const int cfg = pos ? pos[4 * n] : 0;
+    const int l0 = pos ? pos[4 * n + 1] : l0s, o1 = pos ? pos[4 * n + 2] : o1s, o2 = pos ? pos[4 * n + 3] : o2s;
     const int8_t* f = fields + (size_t)cfg * cfg_stride;
     for (int idx = threadIdx.x; idx < g.d_in; idx += blockDim.x) {
         const int sub = idx & 1;

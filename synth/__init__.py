@@ -31,6 +31,13 @@ WORKLOADS = {
 BATCHED = dict(sizes=((6, 2), (9, 1), (12, 1)), twists=4, dtau=0.1, U=3.73, n_stab=10)
 
 
+# Learned block proposals, measured at the plain-GPU size (L = 6, beta t = 6):
+# blocks of b x b cells x T slices, context h cells / ht slices, hidden width,
+# training configurations taken one per sweep from a plain chain.
+LEARNED = dict(L=6, beta=6.0, dtau=0.1, U=3.73, n_delay=32, n_stab=10, b=2, T=2, h=1, ht=1, hidden=64,
+               n_cfg=600, train_steps=2000, batch=256, lr=3e-3)
+
+
 def batched_chains():
     """(L, beta, theta, replica) of every chain of the batched workload."""
     out = []
