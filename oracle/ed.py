@@ -82,7 +82,7 @@ def trotter_averages(lat, K, U, dtau, M):
     N = lat.N
     pairs = bravais_pair_table(lat)
     Z = 0.0
-    acc_d = acc_kin = 0.0
+    acc_d = acc_kin = acc_n1 = acc_n2 = 0.0
     acc_c = {k: 0.0 for k in pairs}
     for nu in range(N + 1):
         for nd in range(N + 1):
@@ -102,6 +102,8 @@ def trotter_averages(lat, K, U, dtau, M):
             ia, ib = np.divmod(np.arange(du * dd), dd)
             diag = X[ia, ib, np.arange(du * dd)].reshape(du, dd)
             Z += diag.sum()
+            acc_n1 += (nu + nd) * diag.sum()                # N is conserved: sector weight x N
+            acc_n2 += (nu + nd) ** 2 * diag.sum()
             acc_d += (docc * diag).sum()
             for key in pairs:
                 acc_c[key] += (czz[key] * diag).sum()
@@ -109,12 +111,15 @@ def trotter_averages(lat, K, U, dtau, M):
             acc_kin += KX[ia, ib, np.arange(du * dd)].sum()
     # with a twist the sector matrices are complex; the traces are real up to rounding
     Z, acc_d, acc_kin = np.real(Z), np.real(acc_d), np.real(acc_kin)
+    acc_n1, acc_n2 = np.real(acc_n1), np.real(acc_n2)
     D = acc_d / Z / N
     ekin = acc_kin / Z
     Czz = np.zeros((lat.L2, lat.L1))
     for (d1, d2), v in acc_c.items():
         Czz[d2, d1] = np.real(v) / Z / (2.0 * lat.Nc)
-    return dict(double_occ=D, energy=(ekin + N * U * D) / N, ekin=ekin / N, Czz=Czz)
+    # Eq. ChiCharge: (beta / N_s) (<N^2> - <N>^2), beta = M dtau
+    chi_e = M * dtau / N * (acc_n2 / Z - (acc_n1 / Z) ** 2)
+    return dict(double_occ=D, energy=(ekin + N * U * D) / N, ekin=ekin / N, Czz=Czz, chi_e=chi_e)
 
 
 def thermal_averages(lat, K, U, beta):

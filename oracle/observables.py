@@ -75,6 +75,14 @@ def measure(model, G):
                 for b in (0, 1):
                     blk = cd[a * Nc:(a + 1) * Nc, b * Nc:(b + 1) * Nc]
                     nk[l2, l1, a, b] = ph @ blk @ ph.conj() / Nc
-    return dict(energy=energy, double_occ=D, ekin=ekin / N, Czz=Czz, S_af=S0, S_af_dk=Sdk,
+    # charge compressibility (Eq. ChiCharge), one-configuration estimator:
+    # chi_e = (beta / N_s) Re( sum_ij <n_i n_j> - N_s^2 ), n = n_up + n_dn, Wick for
+    # every spin pair (the MC average of sum_i <n_i> is N_s at half filling)
+    n_tot = nu + nd
+    nn_sum = np.sum(np.outer(n_tot, n_tot))
+    for Gs in (Gu, Gd):
+        nn_sum = nn_sum + np.sum((I - Gs.T) * Gs)
+    chi_e = float(model.beta / N * np.real(nn_sum - N * N))
+    return dict(energy=energy, double_occ=D, ekin=ekin / N, Czz=Czz, S_af=S0, S_af_dk=Sdk, chi_e=chi_e,
                 m2=S0 / (2.0 * Nc), R_m2=1.0 - Sdk / S0, Czz_half=Czz[0, L1 // 2], nk=nk,
                 density=float(np.mean(nu + nd).real))

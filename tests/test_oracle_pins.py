@@ -239,8 +239,8 @@ def test_hs_sum_equals_trotter_ed():
     """Exhaustive HS sum (oracle weights + Wick) equals the Trotterised Fock-space ED exactly (L=2, 8 sites, M=2)."""
     m = Model(2, U=4.0, beta=0.4, dtau=0.2)
     ref = ed.trotter_averages(m.lat, m.K, m.U, m.dtau, m.M)
-    got = hs_enum.hs_average(m)
-    for k in ("double_occ", "energy", "ekin"):
+    got = hs_enum.hs_average(m, keys=("double_occ", "energy", "ekin", "Czz", "chi_e"))
+    for k in ("double_occ", "energy", "ekin", "chi_e"):
         assert abs(got[k] - ref[k]) < 1e-10
     assert np.abs(got["Czz"] - ref["Czz"]).max() < 1e-10
 
@@ -374,7 +374,19 @@ def test_hs_sum_equals_trotter_ed_twisted():
     e^{-gamma sum s}|det|^2 and complex Wick contractions equals the Trotterised ED."""
     m = Model(2, U=4.0, beta=0.4, dtau=0.2, theta=TW)
     ref = ed.trotter_averages(m.lat, m.K, m.U, m.dtau, m.M)
-    got = hs_enum.hs_average(m)
-    for k in ("double_occ", "energy", "ekin"):
+    got = hs_enum.hs_average(m, keys=("double_occ", "energy", "ekin", "Czz", "chi_e"))
+    for k in ("double_occ", "energy", "ekin", "chi_e"):
         assert abs(got[k] - ref[k]) < 1e-10
     assert np.abs(got["Czz"] - ref["Czz"]).max() < 1e-10
+
+
+@pytest.mark.parametrize("theta", [(0.0, 0.0), TW])
+def test_U0_charge_compressibility_closed_form(theta):
+    """Free fermions: chi_e = (beta / N_s) * 2 sum_lambda f (1 - f) over the
+    single-particle levels (Eq. ChiCharge; two spins, independent modes)."""
+    L, beta = 3, 3.0
+    m = Model(L, U=0.0, beta=beta, dtau=0.1, theta=theta)
+    o = measure(m, m.green_stable(random_field(m.M, m.N, 2), 0, 10))
+    lam = np.linalg.eigvalsh(m.K)
+    f = 1.0 / (1.0 + np.exp(beta * lam))
+    assert abs(o["chi_e"] - beta / m.N * 2.0 * np.sum(f * (1.0 - f))) < 1e-12
