@@ -481,7 +481,7 @@ def run_ours(args):
            "gpu_launches": int(head["launches"]),
            "acceptance": head["accepted"] / max(head["proposed"], 1), "max_stab_drift": head["drift"],
            "kernel_ms_breakdown_sweep": {k: {"launches": v[0], "ms": v[1]} for k, v in head["breakdown"].items()},
-           "observables": {k: head["obs"][k] for k in ("energy", "double_occ", "S_af", "m2", "n_samples")}}
+           "observables": {k: head["obs"][k] for k in ("energy", "double_occ", "S_af", "m2", "chi_e", "n_samples")}}
     if ref64 is not None:
         rel = {k: abs(head["obs"][k] - ref64["obs"][k]) / max(abs(ref64["obs"][k]), 1e-300)
                for k in ("energy", "double_occ", "S_af")}

@@ -122,6 +122,7 @@ typedef struct {
     double S_af_dk;     /* S_zz(Gamma + b1/L1) */
     double R_m2;        /* 1 - S_zz(Gamma + b1/L1) / S_zz(Gamma)            (Eq. CrfRatio) */
     double Czz_half;    /* C_zz(r = floor(L1/2) a1)                         (Eq. SzSzCrF) */
+    double chi_e;       /* (beta / N) (<N^2> - <N>^2), charge compressibility (Eq. ChiCharge) */
     int64_t n_samples;
 } afqmc_obs;
 

@@ -53,7 +53,7 @@ class afqmc_obs(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("double_occ", ctypes.c_double), ("ekin", ctypes.c_double),
                 ("density", ctypes.c_double), ("m2", ctypes.c_double), ("S_af", ctypes.c_double),
                 ("S_af_dk", ctypes.c_double), ("R_m2", ctypes.c_double), ("Czz_half", ctypes.c_double),
-                ("n_samples", ctypes.c_int64)]
+                ("chi_e", ctypes.c_double), ("n_samples", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

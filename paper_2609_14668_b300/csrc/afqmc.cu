@@ -87,7 +87,7 @@ struct afqmc_handle {
     DevStatus* st = nullptr;
     unsigned long long* n_acc = nullptr;
     unsigned long long* drift = nullptr;
-    double *czz = nullptr, *hab = nullptr;                     // per-measurement scratch
+    double *czz = nullptr, *hab = nullptr, *tr2 = nullptr;     // per-measurement scratch
     double *obs_now = nullptr, *czz_now = nullptr, *nk_now = nullptr;
     double *obs_acc = nullptr, *czz_acc = nullptr, *nk_acc = nullptr;
     // block moves (allocated on the first block pass)
@@ -414,15 +414,19 @@ void measure(afqmc_handle* h, const double* G, bool accumulate) {
     half_step(h, G, g);
     const GView gv{g, h->Np, h->N, h->cplx};
     { Scope sc(h, AFQMC_K_MEASURE); k_measure_pairs<<<h->Nc, 128, 0, h->stream>>>(gv, h->L1, h->L2, h->czz, h->hab); }
+    const int nt = (h->Np + 31) / 32;
+    { Scope sc(h, AFQMC_K_MEASURE); k_measure_tr2<<<nt * nt, 256, 0, h->stream>>>(gv, h->tr2); }
     CK(cudaGetLastError());
     if (accumulate) {
         { Scope sc(h, AFQMC_K_MEASURE); k_measure_nk<<<(h->Nc + 127) / 128, 128, 0, h->stream>>>(h->hab, h->L1, h->L2, h->tw1, h->tw2, h->nk_acc, 1); }
-        { Scope sc(h, AFQMC_K_MEASURE); k_measure_scalars<<<1, 256, 0, h->stream>>>(gv, h->czz, h->L1, h->L2, h->p.t, h->p.U, h->tw1,
-                                                    h->bond_ph, h->obs_acc, h->czz_acc, 1, h->obs_count, h->st); }
+        { Scope sc(h, AFQMC_K_MEASURE); k_measure_scalars<<<1, 256, 0, h->stream>>>(gv, h->czz, h->tr2, nt * nt, h->L1, h->L2, h->p.t, h->p.U,
+                                                    h->p.beta, h->tw1, h->bond_ph, h->obs_acc, h->czz_acc, 1,
+                                                    h->obs_count, h->st); }
     } else {
         { Scope sc(h, AFQMC_K_MEASURE); k_measure_nk<<<(h->Nc + 127) / 128, 128, 0, h->stream>>>(h->hab, h->L1, h->L2, h->tw1, h->tw2, h->nk_now, 0); }
-        { Scope sc(h, AFQMC_K_MEASURE); k_measure_scalars<<<1, 256, 0, h->stream>>>(gv, h->czz, h->L1, h->L2, h->p.t, h->p.U, h->tw1,
-                                                    h->bond_ph, h->obs_now, nullptr, 0, nullptr, h->st); }
+        { Scope sc(h, AFQMC_K_MEASURE); k_measure_scalars<<<1, 256, 0, h->stream>>>(gv, h->czz, h->tr2, nt * nt, h->L1, h->L2, h->p.t, h->p.U,
+                                                    h->p.beta, h->tw1, h->bond_ph, h->obs_now, nullptr, 0,
+                                                    nullptr, h->st); }
         CK(cudaMemcpyAsync(h->czz_now, h->czz, sizeof(double) * h->Nc, cudaMemcpyDeviceToDevice, h->stream));
     }
     CK(cudaGetLastError());
@@ -720,6 +724,7 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         h->d_sweep = h->dalloc<unsigned long long>(1);
         CK(cudaMemset(h->d_sweep, 0, sizeof(unsigned long long)));
         h->czz = h->dalloc<double>(Nc);
+        h->tr2 = h->dalloc<double>((size_t)((Np + 31) / 32) * ((Np + 31) / 32));
         h->hab = h->dalloc<double>((size_t)8 * Nc);
         h->obs_now = h->dalloc<double>(OBS_SCALARS);
         h->czz_now = h->dalloc<double>(Nc);
@@ -830,6 +835,7 @@ afqmc_status afqmc_sweep(afqmc_handle* h, int32_t n_sweeps, afqmc_sweep_stats* s
 static void fill_obs(const double* v, long long n, afqmc_obs* out) {
     out->energy = v[0]; out->double_occ = v[1]; out->ekin = v[2]; out->density = v[3];
     out->m2 = v[4]; out->S_af = v[5]; out->S_af_dk = v[6]; out->R_m2 = v[7]; out->Czz_half = v[8];
+    out->chi_e = v[9];
     out->n_samples = n;
 }
 

@@ -14,7 +14,7 @@
 
 namespace afq {
 
-constexpr int OBS_SCALARS = 9;   // energy, D, ekin, density, m2, S_af, S_af_dk, R_m2, Czz_half
+constexpr int OBS_SCALARS = 10;  // energy, D, ekin, density, m2, S_af, S_af_dk, R_m2, Czz_half, chi_e
 
 // Read access to g (N x N physical sites): real, or the embedding of a complex g.
 struct GView {
@@ -98,20 +98,53 @@ __global__ void k_measure_nk(const double* __restrict__ h, int L1, int L2, const
 // Scalars (one CTA).  out[0..8] = energy, D, ekin, density, m2, S_af, S_af_dk,
 // R_m2, Czz_half; czz_acc (optional) accumulates czz; acc != 0 adds into out;
 // count (optional) is incremented.
+// Re tr(g^2) = Re sum_ij g_ij g_ji, one 32 x 32 tile pair per CTA: tile (I, J)
+// and tile (J, I) are read coalesced through shared memory; out[tile] is the
+// tile's partial sum (summed in fixed order by k_measure_scalars).
+__global__ void k_measure_tr2(GView g, double* out) {
+    __shared__ double a_re[32][33], a_im[32][33], b_re[32][33], b_im[32][33];
+    __shared__ double red[33];
+    const int nt = (g.N + 31) / 32;
+    const int I = blockIdx.x / nt, J = blockIdx.x % nt;
+    for (int o = threadIdx.x; o < 32 * 32; o += blockDim.x) {
+        const int r = o / 32, c = o % 32;
+        const int i = I * 32 + r, j = J * 32 + c;
+        const int i2 = J * 32 + r, j2 = I * 32 + c;
+        double2 v = make_double2(0.0, 0.0), w = make_double2(0.0, 0.0);
+        if (i < g.N && j < g.N) v = g.at(i, j);
+        if (i2 < g.N && j2 < g.N) w = g.at(i2, j2);
+        a_re[r][c] = v.x; a_im[r][c] = v.y;
+        b_re[r][c] = w.x; b_im[r][c] = w.y;
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (int o = threadIdx.x; o < 32 * 32; o += blockDim.x) {
+        const int r = o / 32, c = o % 32;
+        // g_ij g_ji with i = I*32 + r, j = J*32 + c; g_ji sits at b[c][r]
+        acc += a_re[r][c] * b_re[c][r] - a_im[r][c] * b_im[c][r];
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = acc;
+}
+
 // Bond phases e^{i Phi_e} of the three bonds A(r) -> B(r + delta_e) (Gauge-I, Sec. III.C).
 struct BondPhases { double2 e[3]; };
 
-__global__ void k_measure_scalars(GView g, const double* __restrict__ czz, int L1, int L2,
-                                  double t, double U, const double2* __restrict__ tw1, BondPhases ph, double* out,
-                                  double* czz_acc, int acc, long long* count, DevStatus* st) {
+__global__ void k_measure_scalars(GView g, const double* __restrict__ czz, const double* __restrict__ tr2, int ntr2,
+                                  int L1, int L2, double t, double U, double beta, const double2* __restrict__ tw1,
+                                  BondPhases ph, double* out, double* czz_acc, int acc, long long* count,
+                                  DevStatus* st) {
     __shared__ double red[33];
     const int Nc = L1 * L2, N = 2 * Nc;
-    double dsum = 0.0, dens = 0.0, kin = 0.0, s0 = 0.0, sdk = 0.0;
+    double dsum = 0.0, dens = 0.0, kin = 0.0, s0 = 0.0, sdk = 0.0, trr = 0.0, tri = 0.0, t2 = 0.0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         const double2 gii = g.at(i, i);
         dsum += gii.x - fma(gii.x, gii.x, gii.y * gii.y);     // Re((1 - g) conj(g))
         dens += (1.0 - gii.x) + gii.x;
+        trr += gii.x;
+        tri += gii.y;
     }
+    for (int q = threadIdx.x; q < ntr2; q += blockDim.x) t2 += tr2[q];
     // bonds A(n1,n2) - B(n1+d1, n2+d2), d in {(0,0), (1,-1), (0,-1)} (Gauge-I, Sec. III.C)
     for (int I = threadIdx.x; I < Nc; I += blockDim.x) {
         const int n1 = I % L1, n2 = I / L1;
@@ -133,6 +166,9 @@ __global__ void k_measure_scalars(GView g, const double* __restrict__ czz, int L
     }
     dsum = block_sum(dsum, red);
     dens = block_sum(dens, red);
+    trr = block_sum(trr, red);
+    tri = block_sum(tri, red);
+    t2 = block_sum(t2, red);
     kin = block_sum(kin, red);
     s0 = block_sum(s0, red);
     sdk = block_sum(sdk, red);
@@ -148,6 +184,8 @@ __global__ void k_measure_scalars(GView g, const double* __restrict__ czz, int L
         v[6] = sdk;
         v[7] = 1.0 - sdk / s0;
         v[8] = czz[(L1 / 2)];
+        // Eq. ChiCharge: sum_ij <n_i n_j> - N^2 = 2 Re(tr g - tr g^2) - 4 (Im tr g)^2 for one field
+        v[9] = beta / N * (2.0 * (trr - t2) - 4.0 * tri * tri);
         bool bad = false;
         for (int q = 0; q < OBS_SCALARS; ++q) {
             if (!isfinite(v[q]) && q != 7) bad = true;

@@ -137,7 +137,7 @@ def test_measure_parity(pkg):
     ch.set_field(f)
     got = ch.measure()
     ref = measure(m, m.green_stable(f, 0, 10))
-    for k in ("energy", "double_occ", "ekin", "density", "m2", "S_af", "S_af_dk", "R_m2", "Czz_half"):
+    for k in ("energy", "double_occ", "ekin", "density", "m2", "S_af", "S_af_dk", "R_m2", "Czz_half", "chi_e"):
         assert abs(got[k] - ref[k]) <= TOL * max(1.0, abs(ref[k])), k
     assert rel_err(got["Czz"], ref["Czz"].reshape(-1)) < TOL
     nk_ref = ref["nk"].reshape(m.lat.Nc, 2, 2)
