@@ -141,3 +141,63 @@ def thermal_averages(lat, K, U, beta):
     D = acc_d / Z / N
     ekin = acc_kin / Z
     return dict(double_occ=D, energy=(ekin + N * U * D) / N, ekin=ekin / N)
+
+
+def trotter_hi_correlation(lat, K, U, dtau, M):
+    """<H_I(tau_l) H_I(0)> and <H_I> under the Trotterised density matrix
+    rho = S^M, S = e^{-dtau H0/2} e^{-dtau H_U} e^{-dtau H0/2}, for l = 0..M:
+    Tr[S^{M-l} H_I S^l H_I] / Tr[S^M] with H_I = sum_i [n_up n_dn - (n_up + n_dn)/2]
+    (diagonal in the occupation basis).  Dense per sector: tiny clusters only."""
+    N = lat.N
+    Z = 0.0
+    hh = np.zeros(M + 1)
+    h1 = 0.0
+    for nu in range(N + 1):
+        for nd in range(N + 1):
+            Ku, Kd, ou, od = _sector_data(K, N, nu, nd)
+            du, dd = Ku.shape[0], Kd.shape[0]
+            Sh = np.kron(sla.expm(-0.5 * dtau * Ku), sla.expm(-0.5 * dtau * Kd))
+            nuu = ou[:, None, :]
+            ndd = od[None, :, :]
+            hi = (nuu * ndd - 0.5 * (nuu + ndd)).sum(axis=2).reshape(-1)
+            S = Sh @ (np.exp(-dtau * U * hi)[:, None] * Sh)
+            P = [np.eye(du * dd)]
+            for _ in range(M):
+                P.append(P[-1] @ S)
+            Z += np.trace(P[M])
+            h1 += np.trace(P[M] * hi[None, :])      # Tr[S^M H_I]
+            for l in range(M + 1):
+                hh[l] += np.real(np.sum((P[M - l] * hi[None, :]) * (P[l] * hi[None, :]).T))
+    Z = np.real(Z)
+    return hh / Z, np.real(h1) / Z
+
+
+def trotter_dDdU(lat, K, U, dtau, M):
+    """dD/dU of the Trotterised density matrix, exactly: with S = Eh e^{-dtau U H_I} Eh
+    (Eh = e^{-dtau H0/2}), d(S^M)/dU = -dtau sum_l S^{M-1-l} (Eh H_I e^{-dtau U H_I} Eh) S^l,
+    so dD/dU = -dtau sum_l cov(D, H_I at the middle of slice l), D = N^-1 sum_i n_up n_dn."""
+    N = lat.N
+    Z = dsum = dmid = 0.0
+    cross = 0.0
+    for nu in range(N + 1):
+        for nd in range(N + 1):
+            Ku, Kd, ou, od = _sector_data(K, N, nu, nd)
+            du, dd = Ku.shape[0], Kd.shape[0]
+            Eh = np.kron(sla.expm(-0.5 * dtau * Ku), sla.expm(-0.5 * dtau * Kd))
+            nuu = ou[:, None, :]
+            ndd = od[None, :, :]
+            hi = (nuu * ndd - 0.5 * (nuu + ndd)).sum(axis=2).reshape(-1)
+            docc = (nuu * ndd).sum(axis=2).reshape(-1) / N
+            eU = np.exp(-dtau * U * hi)
+            S = Eh @ (eU[:, None] * Eh)
+            Smid = Eh @ ((hi * eU)[:, None] * Eh)
+            P = [np.eye(du * dd)]
+            for _ in range(M):
+                P.append(P[-1] @ S)
+            Z += np.trace(P[M])
+            dsum += np.trace(P[M] * docc[None, :])
+            dmid += np.trace(P[M - 1] @ Smid)
+            for l in range(M):
+                cross += np.trace(P[M - 1 - l] @ Smid @ (P[l] * docc[None, :]))
+    Z, dsum, dmid, cross = (np.real(x) for x in (Z, dsum, dmid, cross))
+    return -dtau * (cross / Z - M * (dsum / Z) * (dmid / Z))
