@@ -180,6 +180,20 @@ afqmc_status afqmc_update_slice(afqmc_handle* h, int32_t slice, int32_t pass,
  * at slice l recomputed from scratch. */
 afqmc_status afqmc_det_ratio(afqmc_handle* h, int32_t slice, int32_t site, double out[3]);
 
+/* Time-displaced measurement of the current field (call between sweeps, the
+ * chain at slice 0; M must be even): G(tau, 0), G(0, tau) and G(tau, tau) for
+ * tau = l dtau, l = 0 .. M/2, from the QR-stabilised stacks every n_stab slices
+ * and propagated in between, and the per-field estimator of
+ * <H_I(tau) H_I(0)> (Wick; H_I = sum_i [n_up n_dn - (n_up + n_dn)/2]) on the
+ * symmetric-split Green's functions, accumulated. */
+afqmc_status afqmc_measure_td(afqmc_handle* h);
+
+/* Averages since the last call, then reset: C[l] = <H_I(tau_l) H_I(0)> - <H_I>^2
+ * for l = 0 .. M/2 (may be NULL), dD/dU = -(2/N) int_0^{beta/2} C dtau
+ * (Eq. DouOccDerive) and chi_F = int_0^{beta/2} tau C dtau (Eq. fidelitysusp),
+ * both by the trapezoidal rule over the slice times; n_samples = measurements. */
+afqmc_status afqmc_get_td(afqmc_handle* h, double* C, double* dDdU, double* chiF, int64_t* n_samples);
+
 /* Per-launch CUDA-event timing of the kernel families whose bit (1 << AFQMC_K_*)
  * is set in family_mask; 0 disables timing, AFQMC_TIMING_ALL times every
  * family.  Resets the totals.  Each timed launch records two events on the

@@ -103,6 +103,8 @@ _SIGS = {
                          ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, _DP]),
     "afqmc_block_sweep": ([_H, _H, _P(afqmc_block_stats)]),
     "afqmc_force_slice": ([_H, ctypes.c_int32, _I8P, _DP, _DP]),
+    "afqmc_measure_td": ([_H]),
+    "afqmc_get_td": ([_H, _DP, _DP, _DP, _P(ctypes.c_int64)]),
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -409,6 +411,19 @@ def afqmc_block_sweep(h, net):
     st = afqmc_block_stats()
     _check(_lib.afqmc_block_sweep(h, net, ctypes.byref(st)), h)
     return st
+
+
+def afqmc_measure_td(h):
+    _check(_lib.afqmc_measure_td(h), h)
+
+
+def afqmc_get_td(h):
+    """(C(tau_l) for l = 0..M/2, dD/dU, chi_F, n_samples)."""
+    _, M, _ = afqmc_dims(h)
+    C = np.empty(M // 2 + 1)
+    d, c, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    _check(_lib.afqmc_get_td(h, _dptr(C), ctypes.byref(d), ctypes.byref(c), ctypes.byref(n)), h)
+    return C, d.value, c.value, n.value
 
 
 def afqmc_force_slice(h, slice_, mask, G):

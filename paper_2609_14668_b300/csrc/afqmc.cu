@@ -20,6 +20,7 @@
 #include "learned.cuh"
 #include "linalg.cuh"
 #include "measure.cuh"
+#include "tdgf.cuh"
 #include "update.cuh"
 #include "wrap.cuh"
 
@@ -100,6 +101,11 @@ struct afqmc_handle {
     int* bpos = nullptr;
     size_t bcap_in = 0, bcap_hid = 0, bcap_out = 0, bcap_T = 0;
     uint64_t block_passes = 0;
+    // time-displaced measurement (allocated on first use)
+    double *td_t0 = nullptr, *td_0t = nullptr, *td_tt = nullptr, *td_s[4] = {}, *td_tmp = nullptr;
+    double2 *td_dtt = nullptr, *td_d00 = nullptr;
+    double *td_part = nullptr, *td_hh = nullptr, *td_h = nullptr;
+    long long td_count = 0;
     long long* obs_count = nullptr;
     std::vector<UDTe> Rst, Lst;
     UDTe tmpA, tmpB;               // scratch entries for get_G
@@ -333,7 +339,11 @@ void udt_extend(afqmc_handle* h, const UDTe& in, const UDTe& out, int lo, int hi
 
 // G = (1 + R L)^-1 with R = U_R D_R T_R, L^T = U_L D_L T_L (Loh-Gubernatis split);
 // the well-conditioned middle matrix is solved by LU with partial pivoting.
-void form_green(afqmc_handle* h, const UDTe& R, const UDTe& Lt, double* Gout) {
+// Optionally also the time-displaced G(tau, 0) = U_L Db_L^-1 M^-1 Ds_R T_R and
+// G(0, tau) = -T_L^T Ds_L M^-1 Db_R^-1 U_R^T with the same LU (R = B(tau, 0),
+// L = B(beta, tau)).
+void form_green(afqmc_handle* h, const UDTe& R, const UDTe& Lt, double* Gout, double* Gt0 = nullptr,
+                double* G0t = nullptr) {
     const int n = h->N;
     { Scope sc(h, AFQMC_K_MISC); k_split_scales<<<(n + 255) / 256, 256, 0, h->stream>>>(R.D, h->DbR, h->DsR, n); }
     { Scope sc(h, AFQMC_K_MISC); k_split_scales<<<(n + 255) / 256, 256, 0, h->stream>>>(Lt.D, h->DbL, h->DsL, n); }
@@ -353,6 +363,24 @@ void form_green(afqmc_handle* h, const UDTe& R, const UDTe& Lt, double* Gout) {
     { Scope sc(h, AFQMC_K_QRAUX); k_backsolve<<<cpb_grid(n), 256, cpb_smem(n), h->stream>>>(Mt, Yt, Wt, n, n, h->DbL, h->st); }
     CK(cudaGetLastError());
     gemm(h, Lt.Ut, 1, Wt, 1, Gout, 1.0, 0.0, nullptr, 0, nullptr, 0);
+    const size_t nn = (size_t)n * n;
+    if (G0t) {
+        // Wt holds (Db_L^-1 M^-1 Db_R^-1 U_R^T)^T: scale by D_L = Ds_L Db_L, then -T_L^T (.)
+        { Scope sc(h, AFQMC_K_MISC); k_scale_cols<<<(unsigned)((nn + 255) / 256), 256, 0, h->stream>>>(Wt, Yt, n, Lt.D); }
+        CK(cudaGetLastError());
+        gemm(h, Lt.T, 1, Yt, 1, G0t, -1.0, 0.0, nullptr, 0, nullptr, 0);
+    }
+    if (Gt0) {
+        {
+            dim3 b(32, 8), g((n + 31) / 32, (n + 31) / 32);
+            Scope sc(h, AFQMC_K_QRAUX);
+            k_transpose_scale<<<g, b, 0, h->stream>>>(R.T, Yt, n, n, h->DsR, 0, nullptr, 0);
+        }
+        { Scope sc(h, AFQMC_K_QRAUX); k_fwdsolve_perm<<<cpb_grid(n), 256, cpb_smem(n), h->stream>>>(Mt, h->piv, Yt, n, n); }
+        { Scope sc(h, AFQMC_K_QRAUX); k_backsolve<<<cpb_grid(n), 256, cpb_smem(n), h->stream>>>(Mt, Yt, Wt, n, n, h->DbL, h->st); }
+        CK(cudaGetLastError());
+        gemm(h, Lt.Ut, 1, Wt, 1, Gt0, 1.0, 0.0, nullptr, 0, nullptr, 0);
+    }
 }
 
 void set_identity(afqmc_handle* h, const UDTe& e) {
@@ -537,6 +565,77 @@ void to_host(afqmc_handle* h, const double* dev, double* host, double* stage) {
     { Scope sc(h, AFQMC_K_MISC); k_extract<<<(unsigned)((n2 + 255) / 256), 256, 0, h->stream>>>(dev, (double2*)stage, h->Np); }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(host, stage, sizeof(double2) * n2, cudaMemcpyDeviceToHost, h->stream));
+}
+
+// ------------------------------------------------------------------ time-displaced measurement
+void td_reserve(afqmc_handle* h) {
+    if (h->td_t0) return;
+    const size_t nn = (size_t)h->N * h->N;
+    h->td_t0 = h->dalloc<double>(nn);
+    h->td_0t = h->dalloc<double>(nn);
+    h->td_tt = h->dalloc<double>(nn);
+    h->td_tmp = h->dalloc<double>(nn);
+    for (auto& b : h->td_s) b = h->dalloc<double>(nn);
+    h->td_dtt = h->dalloc<double2>(h->Np);
+    h->td_d00 = h->dalloc<double2>(h->Np);
+    const int nt = (h->Np + 31) / 32;
+    h->td_part = h->dalloc<double>((size_t)nt * nt);
+    h->td_hh = h->dalloc<double>(h->M / 2 + 1);
+    h->td_h = h->dalloc<double>(1);
+    CK(cudaMemsetAsync(h->td_hh, 0, sizeof(double) * (h->M / 2 + 1), h->stream));
+    CK(cudaMemsetAsync(h->td_h, 0, sizeof(double), h->stream));
+}
+
+// accumulate Re sum_ij <A_i(tau_l) A_j(0)> of the current symmetrised matrices
+void td_accumulate(afqmc_handle* h, int l) {
+    const int n = h->N;
+    half_step(h, h->td_tt, h->td_s[1]);
+    half_step(h, h->td_t0, h->td_s[2]);
+    half_step(h, h->td_0t, h->td_s[3]);
+    const GView tt{h->td_s[1], h->Np, n, h->cplx}, t0{h->td_s[2], h->Np, n, h->cplx}, ot{h->td_s[3], h->Np, n, h->cplx};
+    const GView g00{h->td_s[0], h->Np, n, h->cplx};
+    const int nt = (h->Np + 31) / 32;
+    { Scope sc(h, AFQMC_K_MEASURE); k_td_diag<<<(h->Np + 255) / 256, 256, 0, h->stream>>>(tt, g00, h->td_dtt, h->td_d00); }
+    { Scope sc(h, AFQMC_K_MEASURE); k_td_tiles<<<nt * nt, 256, 0, h->stream>>>(t0, ot, h->td_dtt, h->td_d00, h->td_part); }
+    { Scope sc(h, AFQMC_K_MEASURE); k_td_reduce<<<1, 256, 0, h->stream>>>(h->td_part, nt * nt, h->td_d00, h->Np, h->td_hh, l,
+                                                                       h->td_h, l == 0 ? 1 : 0, h->st); }
+    CK(cudaGetLastError());
+}
+
+// One time-displaced measurement of the current field from slice 0 (between
+// sweeps): G(tau, 0), G(0, tau), G(tau, tau) for tau = 0 .. beta/2, recomputed
+// from the stacks every n_stab slices (the R stack is rebuilt on the way, the
+// L stack is the one the last backward pass left), propagated in between.
+void td_measure(afqmc_handle* h) {
+    td_reserve(h);
+    const int n = h->N;
+    const size_t nn = (size_t)n * n;
+    CK(cudaMemcpyAsync(h->td_tt, h->G, sizeof(double) * nn, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->td_t0, h->G, sizeof(double) * nn, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->td_0t, h->G, sizeof(double) * nn, cudaMemcpyDeviceToDevice, h->stream));
+    { Scope sc(h, AFQMC_K_MISC); k_sub_identity<<<(n + 255) / 256, 256, 0, h->stream>>>(h->td_0t, n); }   // G(0, 0+) = G - 1
+    CK(cudaGetLastError());
+    half_step(h, h->G, h->td_s[0]);
+    td_accumulate(h, 0);
+    for (int l = 1; l <= h->M / 2; ++l) {
+        if (l % h->ns == 0) {
+            const int c = l / h->ns;
+            udt_extend(h, h->Rst[c - 1], h->Rst[c], (c - 1) * h->ns + 1, c * h->ns, true);
+            form_green(h, h->Rst[c], h->Lst[c], h->td_tt, h->td_t0, h->td_0t);
+        } else {
+            wrap(h, h->td_tt, l, +1);
+            {
+                dim3 b(32, 8), g((n + 31) / 32, (n + 31) / 32);
+                Scope sc(h, AFQMC_K_MISC);
+                k_transpose_scale<<<g, b, 0, h->stream>>>(h->td_t0, h->td_tmp, n, n, nullptr, 0, nullptr, 0);
+            }
+            CK(cudaGetLastError());
+            launch_rowop(h, h->td_tmp, h->td_t0, n, OP_E, no_scale(), vscale(h, l, +1), true);     // B_l G(tau, 0)
+            launch_rowop(h, h->td_0t, h->td_0t, n, OP_EINV, no_scale(), vscale(h, l, -1), false);  // G(0, tau) B_l^-1
+        }
+        td_accumulate(h, l);
+    }
+    h->td_count += 1;
 }
 
 // ------------------------------------------------------------------ allocation-free slice update
@@ -934,6 +1033,49 @@ afqmc_status afqmc_det_ratio(afqmc_handle* h, int32_t slice, int32_t site, doubl
     { Scope sc(h, AFQMC_K_MISC); k_ratio<<<1, 1, 0, h->stream>>>(gv, site, sv, h->dl_p, h->dl_m, h->ef_p, h->ef_m, o); }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(out, o, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return check_device(h);
+    API_END(h)
+}
+
+afqmc_status afqmc_measure_td(afqmc_handle* h) {
+    API_BEGIN(h)
+    if (h->M % 2) { h->err = "the time-displaced measurement needs an even number of slices (tau up to beta/2)"; return AFQMC_E_INVALID; }
+    td_measure(h);
+    return check_device(h);
+    API_END(h)
+}
+
+afqmc_status afqmc_get_td(afqmc_handle* h, double* C, double* dDdU, double* chiF, int64_t* n_samples) {
+    API_BEGIN(h)
+    const int nl = h->M / 2 + 1;
+    std::vector<double> hh(nl, 0.0);
+    double h1 = 0.0;
+    const long long n = h->td_count;
+    if (h->td_hh && n > 0) {
+        CK(cudaMemcpyAsync(hh.data(), h->td_hh, sizeof(double) * nl, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(&h1, h->td_h, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        afqmc_status s = check_device(h);
+        if (s != AFQMC_OK) return s;
+    }
+    // C(tau) = <H_I(tau) H_I(0)> - <H_I>^2 over the measured fields; trapezoidal integrals
+    // dD/dU = -(2/N) int_0^{beta/2} C, chi_F = int_0^{beta/2} tau C (Eqs. DouOccDerive, fidelitysusp)
+    const double inv = n > 0 ? 1.0 / (double)n : 0.0, hm = h1 * inv;
+    double i0 = 0.0, i1 = 0.0;
+    for (int l = 0; l < nl; ++l) {
+        const double c = hh[l] * inv - hm * hm;
+        if (C) C[l] = c;
+        const double w = (l == 0 || l == nl - 1) ? 0.5 : 1.0;
+        i0 += w * c;
+        i1 += w * c * (l * h->p.dtau);
+    }
+    if (dDdU) *dDdU = -2.0 / h->Np * h->p.dtau * i0;
+    if (chiF) *chiF = h->p.dtau * i1;
+    if (n_samples) *n_samples = n;
+    if (h->td_hh) {
+        CK(cudaMemsetAsync(h->td_hh, 0, sizeof(double) * nl, h->stream));
+        CK(cudaMemsetAsync(h->td_h, 0, sizeof(double), h->stream));
+    }
+    h->td_count = 0;
     return check_device(h);
     API_END(h)
 }
