@@ -59,8 +59,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tau-sweeps", type=int, default=15,
                     help="extra sweeps per chain (after the timed and e2e ones) for the autocorrelation time")
-    ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
-                    help="1: split-TF32 tensor-core flush (the L=24 precision workload); 0: plain FP64")
+    ap.add_argument("--precision", type=int, default=3, choices=[0, 1, 2, 3],
+                    help="bit 0: split-TF32 tensor-core flush (the L=24 precision workload); bit 1: stabilisation "
+                         "products on the BF16 tensor cores with FP64 accuracy (Ozaki); 0: plain FP64")
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 sweep")
     ap.add_argument("--chains", type=int, default=3,
                     help="independent chains per GPU, each on its own CUDA stream and host thread "
@@ -371,7 +372,7 @@ def roofline_of(res, N, precision):
     Nc = N // 2
     nl, tms = timing[fam]
     acc_per_update = accepted / max(timing["update"][0], 1)
-    if fam == "update" and precision == 1:
+    if fam == "update" and (precision & 1):
         # flush on the tensor cores: 2 N^2 algorithmic flops per accepted flip, each
         # product done as three TF32 products (split-TF32), so the peak is TF32 / 3
         fl = 2.0 * N * N * acc_per_update
@@ -471,7 +472,10 @@ def run_ours(args):
     out = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if args.precision == 0 else "f64 (flush: tf32x3, f32 accumulate)",
+           "dtype": {0: "f64", 1: "f64 (flush: tf32x3, f32 accumulate)",
+                     2: "f64 (stabilisation products: bf16 Ozaki, FP64-accurate)",
+                     3: "f64 (flush: tf32x3, f32 accumulate; stabilisation products: bf16 Ozaki, FP64-accurate)"}
+                    [args.precision],
            "data": "synthetic (random initial Ising field from the seed; no dataset)",
            "config": {"workload": key, "L": w["L"], "N_sites": N, "beta": w["beta"], "dtau": w["dtau"], "M": M,
                       "U": w["U"], "n_delay": w["n_delay"], "n_stab": w["n_stab"], "precision": args.precision,

@@ -73,10 +73,13 @@ typedef struct {
     int32_t hs_channel;    /* 0 = spin channel HS-s^z (Eq. SzHS); only 0 supported */
     int32_t n_delay;       /* delay rank n_d >= 1; 1 is the local Sherman-Morrison update */
     int32_t n_stab;        /* slices between QR recomputations of G; M % n_stab == 0 */
-    int32_t precision;     /* 0 = FP64 everywhere; 1 = delayed-update flush G -= X Y as three TF32
-                              tensor-core products (hi*hi + hi*lo + lo*hi, FP32 accumulate)
-                              subtracted from the FP64 G; ratios, x/y recursion, wraps,
-                              stabilisation and measurements stay FP64 */
+    int32_t precision;     /* bit mask; 0 = FP64 everywhere.  Bit 0: delayed-update flush
+                              G -= X Y as three TF32 tensor-core products (hi*hi + hi*lo + lo*hi,
+                              FP32 accumulate) subtracted from the FP64 G.  Bit 1: the matrix
+                              products of the stabilisation (stack extension, middle matrix and G
+                              recomputation) on the BF16 tensor cores by the Ozaki scheme,
+                              FP64-accurate (8 digits of 7 bits, exact FP32 class sums).  Ratios,
+                              x/y recursion, wraps, QR, LU and measurements stay FP64 */
     int32_t measure;       /* 1: accumulate observables at every recomputation of G in a sweep */
     int32_t chain;         /* chain index: selects the random stream */
     int32_t device;        /* CUDA device ordinal */

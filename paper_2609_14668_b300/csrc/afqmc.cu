@@ -20,6 +20,7 @@
 #include "learned.cuh"
 #include "linalg.cuh"
 #include "measure.cuh"
+#include "ozaki.cuh"
 #include "tdgf.cuh"
 #include "update.cuh"
 #include "wrap.cuh"
@@ -68,6 +69,10 @@ struct afqmc_handle {
     bool own_stream = false;
     int sms = 0;
     int upd_grid = 0;              // CTAs of the cooperative slice kernel
+    // precision bit 1: digit planes and exponents of the Ozaki products
+    __nv_bfloat16 *ozA = nullptr, *ozB = nullptr;
+    int *ozea = nullptr, *ozeb = nullptr;
+    int ozKpad = 0;
     bool in_batch = false;         // owned by an afqmc_batch (no per-launch timing)
     bool broken = false;
     std::string err;
@@ -249,8 +254,38 @@ DiagScale vscale(afqmc_handle* h, int l, int sign) {   // e^{sign gamma s_l}
     return sign > 0 ? DiagScale{s, h->egp, h->egm} : DiagScale{s, h->egm, h->egp};
 }
 
+// C = alpha rs .* (op(A) op(B)) .* cs + beta C on the BF16 tensor cores, FP64-accurate (ozaki.cuh)
+void gemm_oz(afqmc_handle* h, const double* A, int transA, const double* B, int transB, double* C, double alpha,
+             double beta, const double* rs, int rs_inv, const double* cs, int cs_inv) {
+    const int n = h->N, Kp = h->ozKpad;
+    // the digits are cut from rows: op(A) rows, and op(B)^T rows (= B rows when transB);
+    // the other cases go through a transposed copy in the scratch matrix Wk[4]
+    auto split = [&](const double* X, bool transpose, __nv_bfloat16* out, int* ex) {
+        const double* src = X;
+        if (transpose) {
+            dim3 b(32, 8), gr((n + 31) / 32, (n + 31) / 32);
+            Scope sc(h, AFQMC_K_GEMM);
+            k_transpose_scale<<<gr, b, 0, h->stream>>>(X, h->Wk[4], n, n, nullptr, 0, nullptr, 0);
+            src = h->Wk[4];
+        }
+        Scope sc(h, AFQMC_K_GEMM);
+        k_oz_split<<<(n * 32 + 255) / 256, 256, 0, h->stream>>>(src, n, n, n, out, Kp, ex);
+    };
+    split(A, transA != 0, h->ozA, h->ozea);
+    split(B, transB == 0, h->ozB, h->ozeb);
+    OzArgs g{h->ozA, h->ozB, h->ozea, h->ozeb, n, n, Kp, C, n, alpha, beta, rs, cs, rs_inv, cs_inv, h->st};
+    dim3 grid((n + OZ_TN - 1) / OZ_TN, (n + OZ_TM - 1) / OZ_TM);
+    Scope sc(h, AFQMC_K_GEMM);
+    k_oz_gemm<<<grid, 256, oz_smem_bytes(), h->stream>>>(g);
+    CK(cudaGetLastError());
+}
+
 void gemm(afqmc_handle* h, const double* A, int transA, const double* B, int transB, double* C, double alpha,
           double beta, const double* rs, int rs_inv, const double* cs, int cs_inv, int a_upper = 0) {
+    if (h->p.precision & 2) {
+        gemm_oz(h, A, transA, B, transB, C, alpha, beta, rs, rs_inv, cs, cs_inv);
+        return;
+    }
     const int n = h->N;
     GemmArgs g{A, B, C, n, n, n, n, n, n, transA, transB, alpha, beta, rs, cs, rs_inv, cs_inv, a_upper};
     dim3 grid((n + GT - 1) / GT, (n + GT - 1) / GT);
@@ -302,7 +337,7 @@ size_t update_smem(int W, int nd, int precision, int N = AFQMC_NOALLOC_MAX_N, in
     const size_t jpb = (size_t)((N + grid - 1) / grid);
     b = std::max(b, sizeof(double) * (2 * (size_t)nd * jpb + 2 * (size_t)nd * W + 2 * (size_t)W * W));   // phase C staging
     size_t f = sizeof(double) * 2 * (size_t)nd * 32;
-    if (precision == 1) {
+    if (precision & 1) {
         f = std::max(f, sizeof(uint32_t) * 4 * (size_t)TCK * TCT);     // TF32 operands of one K round
         f = std::max(f, sizeof(float) * (size_t)TCT * (TCT + 1));      // accumulator tile
     }
@@ -705,7 +740,8 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
     if (!(P.theta1 >= 0.0 && P.theta1 < 1.0 && P.theta2 >= 0.0 && P.theta2 < 1.0))
         return bad("twist angles theta1, theta2 must be in [0, 1)");
     if (P.hs_channel != 0) return bad("only the spin channel (hs_channel = 0) is supported");
-    if (P.precision != 0 && P.precision != 1) return bad("precision must be 0 (FP64) or 1 (split-TF32 flush)");
+    if (P.precision < 0 || P.precision > 3)
+        return bad("precision must be 0..3 (bit 0: split-TF32 flush, bit 1: tensor-core FP64-accurate stabilisation products)");
     const double Mr = P.beta / P.dtau;
     const int M = (int)std::llround(Mr);
     if (M < 1 || std::fabs(M * P.dtau - P.beta) > 1e-9) return bad("beta must be an integer multiple of dtau");
@@ -811,6 +847,17 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         h->Dp = h->dalloc<double>(N);
         h->sgn = h->dalloc<double>(N);
         h->tau = h->dalloc<double>(N);
+        if (P.precision & 2) {
+            h->ozKpad = (N + OZ_KC - 1) / OZ_KC * OZ_KC;
+            h->ozA = h->dalloc<__nv_bfloat16>((size_t)OZ_S * N * h->ozKpad);
+            h->ozB = h->dalloc<__nv_bfloat16>((size_t)OZ_S * N * h->ozKpad);
+            h->ozea = h->dalloc<int>(N);
+            h->ozeb = h->dalloc<int>(N);
+            CK(raise_smem_limit((const void*)k_oz_gemm, oz_smem_bytes()));
+            int occ_oz = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_oz, k_oz_gemm, 256, oz_smem_bytes()));
+            if (occ_oz < 1) throw CudaFail{AFQMC_E_INVALID, "tensor-core product kernel does not fit on an SM"};
+        }
         h->DbR = h->dalloc<double>(N); h->DsR = h->dalloc<double>(N);
         h->DbL = h->dalloc<double>(N); h->DsL = h->dalloc<double>(N);
         h->flags = h->dalloc<unsigned int>(N);

@@ -45,7 +45,7 @@ struct UpdArgs {
     uint64_t ctr_stride;
     unsigned long long* n_acc;
     DevStatus* st;
-    int precision;                // 0: FP64 flush; 1: split-TF32 tcgen05 flush, FP32 accumulate
+    int precision;                // bit 0: split-TF32 tcgen05 flush (FP32 accumulate); else FP64 flush
     int pair;                     // 1: G is the real 2Np x 2Np embedding of a complex G (twist)
     int Np;                       // physical sites (field length); N = 2 Np when pair
     // forced mode (block moves): flip exactly the sites with force[i] != 0, no
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_mbar;
     uint32_t tmem = 0, mbar = 0, phase = 0;
-    if (a.precision == 1) {
+    if ((a.precision & 1)) {
         if (threadIdx.x < 32) {
             asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                          :: "r"(smem_u32(&s_tmem)), "r"(TCT) : "memory");
@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
         const bool done = (c1 >= (a.pair ? a.Np : N));
         // ------------------------------------------------------------ phase F
         if (k > 0 && (k == nd || done)) {
-            if (a.precision == 1) {
+            if ((a.precision & 1)) {
                 const int nt = (N + TCT - 1) / TCT;
                 for (int tile = blockIdx.x; tile < nt * nt; tile += gridDim.x)
                     if (!flush_tile_tcgen05(a, k, (tile / nt) * TCT, (tile % nt) * TCT,
@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
             if (!grid_barrier(a.st, 4)) break;
         }
     }
-    if (a.precision == 1) {
+    if ((a.precision & 1)) {
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         if (threadIdx.x < 32)
