@@ -276,7 +276,7 @@ void gemm_oz(afqmc_handle* h, const double* A, int transA, const double* B, int 
     OzArgs g{h->ozA, h->ozB, h->ozea, h->ozeb, n, n, Kp, C, n, alpha, beta, rs, cs, rs_inv, cs_inv, h->st};
     dim3 grid((n + OZ_TN - 1) / OZ_TN, (n + OZ_TM - 1) / OZ_TM);
     Scope sc(h, AFQMC_K_GEMM);
-    k_oz_gemm<<<grid, 256, oz_smem_bytes(), h->stream>>>(g);
+    k_oz_gemm<<<grid, OZ_THREADS, oz_smem_bytes(), h->stream>>>(g);
     CK(cudaGetLastError());
 }
 
@@ -855,7 +855,7 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
             h->ozeb = h->dalloc<int>(N);
             CK(raise_smem_limit((const void*)k_oz_gemm, oz_smem_bytes()));
             int occ_oz = 0;
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_oz, k_oz_gemm, 256, oz_smem_bytes()));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_oz, k_oz_gemm, OZ_THREADS, oz_smem_bytes()));
             if (occ_oz < 1) throw CudaFail{AFQMC_E_INVALID, "tensor-core product kernel does not fit on an SM"};
         }
         h->DbR = h->dalloc<double>(N); h->DsR = h->dalloc<double>(N);

@@ -17,14 +17,15 @@
 // products are integers of at most 14 bits; summed over 320 values of k the
 // class sums stay below 2^24 (class 0: 320 * 2^14; class w >= 1: 320 *
 // (2 * 2^13 + (w-1) * 2^12) <= 1.4e7), so the FP32 accumulation is exact.  After
-// every 320 values of k the classes are read out and added, scaled by their
+// every 320 values of k (10 chunks of 32) the classes are read out and added, scaled by their
 // power of two, into FP64 registers: the only rounding is that of the final
 // FP64 sums, as in an FP64 GEMM.
 //
-// Tile: 128 x 64 outputs per CTA (m128n64k16 MMAs), K staged 64 at a time for
-// all 8 digits of both operands (128 KB + 64 KB of shared memory, canonical
-// no-swizzle K-major layout: 8-row x 16-byte core matrices, LBO 128 B,
-// SBO = 64 * 2 * 8 B), one thread issues the MMAs, completion on an mbarrier
+// Tile: 128 x 64 outputs per CTA (m128n64k16 MMAs), K staged 32 at a time for
+// all 8 digits of both operands (64 KB + 32 KB), double-buffered so that the
+// copies of chunk c+1 (cp.async) overlap the MMAs of chunk c; canonical
+// no-swizzle K-major layout (8-row x 16-byte core matrices, LBO 128 B,
+// SBO = 32 * 2 * 8 B); one thread issues the MMAs, completion on an mbarrier
 // (bounded wait), tensor memory freed on every exit path.
 #pragma once
 #include <cuda_bf16.h>
@@ -35,7 +36,7 @@ namespace afq {
 
 constexpr int OZ_S = 8;          // digits per operand
 constexpr int OZ_BITS = 7;
-constexpr int OZ_TM = 128, OZ_TN = 64, OZ_KC = 64, OZ_WIN = 5;   // tile, K chunk, chunks per exact window
+constexpr int OZ_TM = 128, OZ_TN = 64, OZ_KC = 32, OZ_WIN = 10;  // tile, K chunk, chunks per exact window
 constexpr int OZ_CLASSES = 8;    // w = s + t = 0..7
 constexpr uint32_t IDESC_BF16_128x64 =
     (1u << 4)                             // D format: F32
@@ -43,9 +44,9 @@ constexpr uint32_t IDESC_BF16_128x64 =
     | ((uint32_t)(OZ_TN >> 3) << 17)      // N / 8
     | ((uint32_t)(OZ_TM >> 4) << 24);     // M / 16
 
-inline size_t oz_smem_bytes() {
-    return (size_t)OZ_S * (OZ_TM + OZ_TN) * OZ_KC * 2 + 1024;
-}
+constexpr size_t OZ_STAGE = (size_t)OZ_S * (OZ_TM + OZ_TN) * OZ_KC * 2;   // one K chunk of all digits
+
+inline size_t oz_smem_bytes() { return 2 * OZ_STAGE + 1024; }   // double-buffered
 
 // rows of X (rows x K, row-major, leading dimension ld) into OZ_S digit planes
 // out[s][row][0..Kpad) (BF16, zero beyond K) and the row exponents ex[row];
@@ -103,14 +104,14 @@ __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uin
         :: "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(IDESC_BF16_128x64), "r"(acc));
 }
 
-__global__ void __launch_bounds__(256, 1) k_oz_gemm(OzArgs g) {
+constexpr int OZ_THREADS = 512;
+
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(OzArgs g) {
     extern __shared__ __align__(1024) unsigned char oz_smem[];
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ int s_fail;
     const int i0 = blockIdx.y * OZ_TM, j0 = blockIdx.x * OZ_TN;
-    unsigned char* Asm = oz_smem;                                   // OZ_S x 128 x 64 BF16
-    unsigned char* Bsm = oz_smem + (size_t)OZ_S * OZ_TM * OZ_KC * 2; // OZ_S x 64 x 64 BF16
     if (threadIdx.x < 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(&s_tmem)), "r"(512) : "memory");
@@ -128,19 +129,27 @@ __global__ void __launch_bounds__(256, 1) k_oz_gemm(OzArgs g) {
     uint32_t phase = 0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = 32 * (warp & 3) + lane;          // TMEM lane = output row of the tile
-    const int cbase = 32 * (warp >> 2);              // warps w, w+4 split the 64 columns
-    double acc[32];
+    const int cbase = 16 * (warp >> 2);              // warps w, w+4, w+8, w+12 split the 64 columns
+    // exact integer sums of classes 0..3 (each < 4 * 2^24 over K <= 1152... < 2^31 for K <= 40960)
+    // and one FP32 sum of classes 4..7 weighted 2^-7(w-4) (its rounding is below 2^-52 of class 0)
+    int iacc[4][16];
+    float facc[16];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) acc[q] = 0.0;
+    for (int q = 0; q < 16; ++q) {
+        iacc[0][q] = iacc[1][q] = iacc[2][q] = iacc[3][q] = 0;
+        facc[q] = 0.0f;
+    }
     const size_t planeA = (size_t)g.m * g.Kpad, planeB = (size_t)g.n * g.Kpad;
     const int nchunks = g.Kpad / OZ_KC;
-    for (int c = 0; c < nchunks; ++c) {
+
+    // stage chunk c of all digits into buffer c & 1: asynchronous 16-byte copies,
+    // zero-filled outside the matrix
+    auto stage = [&](int c) {
+        unsigned char* Asm = oz_smem + (size_t)(c & 1) * OZ_STAGE;
+        unsigned char* Bsm = Asm + (size_t)OZ_S * OZ_TM * OZ_KC * 2;
         const int k0 = c * OZ_KC;
-        // ---- stage all digits of both operands for this K chunk (16-byte vectors)
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        // asynchronous 16-byte copies (all in flight at once), zero-filled outside the matrix
         constexpr int VA = OZ_S * OZ_TM * (OZ_KC / 8), VB = OZ_S * OZ_TN * (OZ_KC / 8);
+#pragma unroll 1
         for (int v = threadIdx.x; v < VA + VB; v += blockDim.x) {
             const bool isA = v < VA;
             const int u = isA ? v : v - VA;
@@ -158,19 +167,42 @@ __global__ void __launch_bounds__(256, 1) k_oz_gemm(OzArgs g) {
                          :: "r"(smem_u32(dst)), "l"(src), "r"(in ? 16 : 0) : "memory");
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
+    };
+
+    stage(0);
+    bool pending = false;        // MMAs of the previous chunk not waited for yet
+    for (int c = 0; c < nchunks; ++c) {
+        // the buffer chunk c+1 will fill was read by the MMAs of chunk c-1
+        if (pending) {
+            if (!mbar_wait_bounded(mbar, phase)) { s_fail = 1; flag_error(g.st, DERR_TIMEOUT, 600); }
+            phase ^= 1u;
+            pending = false;
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (s_fail) break;
+        if (c + 1 < nchunks) {
+            stage(c + 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");     // chunk c has landed
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        // ---- 36 digit products into the 8 class accumulators
+        // ---- 36 digit products of chunk c into the 8 class accumulators
         const int cw = c % OZ_WIN;          // chunk within the exact window
         if (threadIdx.x == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t sbo = (uint32_t)(OZ_KC * 16);
+            const uint32_t abase = smem_u32(oz_smem + (size_t)(c & 1) * OZ_STAGE);
+            const uint32_t bbase = abase + (uint32_t)(OZ_S * OZ_TM * OZ_KC * 2);
+#pragma unroll 1
             for (int w = 0; w < OZ_CLASSES; ++w)
+#pragma unroll 1
                 for (int s = 0; s <= w; ++s) {
-                    const int t = w - s;
-                    const uint32_t a0 = smem_u32(Asm + (size_t)s * OZ_TM * OZ_KC * 2);
-                    const uint32_t b0 = smem_u32(Bsm + (size_t)t * OZ_TN * OZ_KC * 2);
+                    const uint32_t a0 = abase + (uint32_t)(s * OZ_TM * OZ_KC * 2);
+                    const uint32_t b0 = bbase + (uint32_t)((w - s) * OZ_TN * OZ_KC * 2);
+#pragma unroll
                     for (int kk = 0; kk < OZ_KC / 16; ++kk) {
                         const uint32_t ko = (uint32_t)(kk * 256);
                         const uint32_t accf = (cw > 0 || s > 0 || kk > 0) ? 1u : 0u;
@@ -181,44 +213,59 @@ __global__ void __launch_bounds__(256, 1) k_oz_gemm(OzArgs g) {
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(mbar) : "memory");
         }
-        if (!mbar_wait_bounded(mbar, phase)) { s_fail = 1; flag_error(g.st, DERR_TIMEOUT, 600); }
-        phase ^= 1u;
-        __syncthreads();
-        if (s_fail) break;
-        // ---- end of an exact window: read the classes out into FP64
+        pending = true;
+        // ---- end of an exact window: wait for the MMAs, read the classes out into FP64
         if (cw == OZ_WIN - 1 || c == nchunks - 1) {
+            if (!mbar_wait_bounded(mbar, phase)) { s_fail = 1; flag_error(g.st, DERR_TIMEOUT, 601); }
+            phase ^= 1u;
+            pending = false;
+            __syncthreads();
+            if (s_fail) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll 1
+#pragma unroll
             for (int w = 0; w < OZ_CLASSES; ++w) {
-                uint32_t v[32];
+                uint32_t v[16];
                 const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(w * OZ_TN + cbase);
                 asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
                       "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
-                      "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
-                      "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                      "=r"(v[14]), "=r"(v[15])
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                const double sc = ldexp(1.0, -OZ_BITS * (w + 2));
+                if (w < 4) {
 #pragma unroll
-                for (int q = 0; q < 32; ++q) acc[q] = fma((double)__uint_as_float(v[q]), sc, acc[q]);
+                    for (int q = 0; q < 16; ++q) iacc[w][q] += __float2int_rn(__uint_as_float(v[q]));
+                } else {
+                    const float sc = ldexpf(1.0f, -OZ_BITS * (w - 4));
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) facc[q] = fmaf(__uint_as_float(v[q]), sc, facc[q]);
+                }
             }
         }
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     // ---- epilogue through shared memory (coalesced rows of C)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (!s_fail) {
         constexpr int CLD = OZ_TN + 1;
         double* ct = reinterpret_cast<double*>(oz_smem);
+        const double s0 = ldexp(1.0, -2 * OZ_BITS), s1 = ldexp(1.0, -3 * OZ_BITS), s2 = ldexp(1.0, -4 * OZ_BITS),
+                     s3 = ldexp(1.0, -5 * OZ_BITS), s4 = ldexp(1.0, -6 * OZ_BITS);
 #pragma unroll
-        for (int q = 0; q < 32; ++q) ct[row * CLD + cbase + q] = acc[q];
+        for (int q = 0; q < 16; ++q) {
+            // smallest terms first
+            double v = (double)facc[q] * s4;
+            v = fma((double)iacc[3][q], s3, v);
+            v = fma((double)iacc[2][q], s2, v);
+            v = fma((double)iacc[1][q], s1, v);
+            v = fma((double)iacc[0][q], s0, v);
+            ct[row * CLD + cbase + q] = v;
+        }
         __syncthreads();
-        for (int r = warp; r < OZ_TM; r += 8) {
+        for (int r = warp; r < OZ_TM; r += OZ_THREADS / 32) {
             const int gi = i0 + r;
             if (gi >= g.m) break;
             double ri = g.alpha * ldexp(1.0, g.ea[gi]);
