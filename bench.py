@@ -159,8 +159,9 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": key, "L": w["L"], "N_sites": N, "M": M, "U": w["U"], "dtau": w["dtau"],
-                      "n_delay": w["n_delay"], "n_stab": w["n_stab"]},
+           "config": {"workload": key, "L": w["L"], "N_sites": N, "beta": w["beta"], "dtau": w["dtau"], "M": M,
+                      "U": w["U"], "n_delay": w["n_delay"], "n_stab": w["n_stab"], "precision": 0,
+                      "parallelism": "host cores (numpy/BLAS threads)"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
                             "sample": (f"each step: one wrap + one slice update ({N} proposals) + one "
                                        f"stabilisation of the FP64 numpy oracle; value = N / (t_slice + "
