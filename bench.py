@@ -63,6 +63,8 @@ def parse():
                     help="bit 0: split-TF32 tensor-core flush (the L=24 precision workload); bit 1: stabilisation "
                          "products on the BF16 tensor cores with FP64 accuracy (Ozaki); 0: plain FP64")
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 sweep")
+    ap.add_argument("--update-ctas", type=int, default=0,
+                    help="CTAs of the cooperative slice kernel per chain (0: one per SM)")
     ap.add_argument("--chains", type=int, default=3,
                     help="independent chains per GPU, each on its own CUDA stream and host thread "
                          "(3 saturates the L=24 workload: 2 -> 260k, 3 -> 289k, 4 -> 289k updates/s)")
@@ -254,7 +256,7 @@ def time_chain(pkg, torch, args, key, precision, rank, world, dev, dist, stream)
     for c in range(C):
         params = pkg.make_params(L=w["L"], beta=w["beta"], dtau=w["dtau"], U=w["U"], n_delay=w["n_delay"],
                                  n_stab=w["n_stab"], seed=1000 + rank, chain=rank * C + c, measure=1,
-                                 device=dev, precision=precision)
+                                 device=dev, precision=precision, update_ctas=args.update_ctas)
         chains.append(pkg.Chain(params, stream=streams[c].cuda_stream))
     ch = chains[0]
 
@@ -483,7 +485,8 @@ def run_ours(args):
            "data": "synthetic (random initial Ising field from the seed; no dataset)",
            "config": {"workload": key, "L": w["L"], "N_sites": N, "beta": w["beta"], "dtau": w["dtau"], "M": M,
                       "U": w["U"], "n_delay": w["n_delay"], "n_stab": w["n_stab"], "precision": args.precision,
-                      "chains_per_gpu": max(1, args.chains), "parallelism": f"replicas{world}",
+                      "chains_per_gpu": max(1, args.chains), "update_ctas": args.update_ctas or "one per SM",
+                      "parallelism": f"replicas{world}",
                       "l2": "no flush: a sweep streams the UDT stacks (1.3 GB) through the 126 MB L2"},
            "roofline": roofline_of(head, N, args.precision),
            "gpu_launches": int(head["launches"]),
