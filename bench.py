@@ -143,7 +143,7 @@ def cpu_baseline(key):
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if not reports(rank):
         return
     key = args.workload
     w, N, M = workload_config(key)
@@ -244,6 +244,32 @@ def algorithmic_flops(family, N, Nc, accepted_per_update):
     return None
 
 
+# --------------------------------------------------------------------------- ranks
+def rank_chains(rank, chains):
+    """Chains of one rank: whole independent chains per rank (weak scaling), so
+    the data path has no collective.  Returns (seed, chain indices); the chain
+    index selects the random stream, so every (rank, chain) pair is a distinct
+    Markov chain."""
+    return 1000 + rank, [rank * chains + c for c in range(chains)]
+
+
+def combine_ranks(dist, ms, proposed, device):
+    """Whole-job numbers: the slowest rank's time (max) and all ranks' proposals (sum)."""
+    import torch
+    if dist is None:
+        return ms, float(proposed)
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([float(proposed)], dtype=torch.float64, device=device)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(p.item())
+
+
+def reports(rank):
+    """Only rank 0 prints the JSON line (and runs the CPU reference arm)."""
+    return rank == 0
+
+
 def time_chain(pkg, torch, args, key, precision, rank, world, dev, dist, stream):
     """Create C chains (one CUDA stream and one host thread each), run W warm-up
     sweeps, time K sweeps of every chain with CUDA events on the chains' streams
@@ -253,9 +279,10 @@ def time_chain(pkg, torch, args, key, precision, rank, world, dev, dist, stream)
     C = max(1, args.chains)
     streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(C - 1)]
     chains = []
+    seed, idx = rank_chains(rank, C)
     for c in range(C):
         params = pkg.make_params(L=w["L"], beta=w["beta"], dtau=w["dtau"], U=w["U"], n_delay=w["n_delay"],
-                                 n_stab=w["n_stab"], seed=1000 + rank, chain=rank * C + c, measure=1,
+                                 n_stab=w["n_stab"], seed=seed, chain=idx[c], measure=1,
                                  device=dev, precision=precision, update_ctas=args.update_ctas)
         chains.append(pkg.Chain(params, stream=streams[c].cuda_stream))
     ch = chains[0]
@@ -330,14 +357,7 @@ def time_chain(pkg, torch, args, key, precision, rank, world, dev, dist, stream)
     obs = ch.observables()
     for c in range(1, C):
         chains[c].observables()
-    ms_max, total_proposed = ms, proposed
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-        p = torch.tensor([float(proposed)], dtype=torch.float64, device=dev)
-        dist.all_reduce(p, op=dist.ReduceOp.SUM)
-        total_proposed = float(p.item())
+    ms_max, total_proposed = combine_ranks(dist, ms, proposed, dev)
     return dict(chain=ch, chains=chains, run_all=run_all, ms=ms_max, value=total_proposed / (ms_max / 1e3), proposed=proposed,
                 total_proposed=total_proposed, accepted=accepted, launches=launches, drift=drift,
                 timing=timing, breakdown=breakdown, dominant=dominant, obs=obs, clocks=ck, barrier=barrier)
@@ -444,11 +464,8 @@ def run_ours(args):
         barrier()
         wall = time.perf_counter() - t0
         nbytes = sum(nb)
-        e2e_val = head["proposed"] / wall
-        if dist is not None:
-            t = torch.tensor([wall], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_val = head["total_proposed"] / float(t.item())
+        wall_max, total = combine_ranks(dist, wall, head["proposed"], dev)
+        e2e_val = total / wall_max
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": nbytes}
 
     # autocorrelation: per-sweep energy and m^2 of every chain (e2e sweeps + extra ones)
@@ -512,7 +529,7 @@ def run_ours(args):
         out["cpu_baseline"] = cpu_baseline(key)
     for c in head["chains"]:
         c.close()
-    if rank == 0:
+    if reports(rank):
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
@@ -531,6 +548,10 @@ def run_batched(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dev = local if world > 1 else 0
     torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl")
     spec = batched_chains()
 
     def params(i, L, beta, th, nd, ct):
@@ -561,7 +582,8 @@ def run_batched(args):
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - t0
     ck = clocks.stop()
-    value = st.proposed / wall
+    wall, total = combine_ranks(dist, wall, st.proposed, dev)
+    value = total / wall
     # the same chains swept one after another with the plain per-chain call
     singles = [pkg.Chain(p) for p in plist]
     torch.cuda.synchronize(dev)
@@ -579,7 +601,9 @@ def run_batched(args):
         obs = [batch.chains[i].observables() for i, c in enumerate(spec) if c[0] == L]
         avg[f"L{L}"] = {k: statistics.fmean([o[k] for o in obs]) for k in ("energy", "double_occ", "S_af")}
     batch.close()
-    if rank != 0:
+    if dist is not None:
+        dist.destroy_process_group()
+    if not reports(rank):
         return
     out = {"metric": "HS-field updates/s, batched twist-averaging chains (64 chains, L in {6,9,12}, 16 twists)",
            "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
