@@ -848,6 +848,9 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         h->sgn = h->dalloc<double>(N);
         h->tau = h->dalloc<double>(N);
         if (P.precision & 2) {
+            // the 32-bit class sums of the product kernel hold every exact window of K <= 2048
+            static_assert(((PRE * 256 + OZ_KC * OZ_WIN - 1) / (OZ_KC * OZ_WIN)) * (1ll << 24) < (1ll << 31),
+                          "class sums of the largest lattice overflow 32 bits");
             h->ozKpad = (N + OZ_KC - 1) / OZ_KC * OZ_KC;
             h->ozA = h->dalloc<__nv_bfloat16>((size_t)OZ_S * N * h->ozKpad);
             h->ozB = h->dalloc<__nv_bfloat16>((size_t)OZ_S * N * h->ozKpad);
