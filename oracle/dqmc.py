@@ -1,21 +1,28 @@
-"""Finite-temperature AFQMC (DQMC) for the half-filled honeycomb Hubbard model,
-spin-channel Ising field (HS-s^z): periodic boundaries (the real FP64 path) or
-twisted boundaries (Sec. III.C: Peierls phases on the bonds, complex G).
+"""Finite-temperature AFQMC (DQMC) for the half-filled honeycomb Hubbard model:
+periodic boundaries or twisted boundaries (Sec. III.C: Peierls phases on the
+bonds, complex G), with the Ising field in the spin channel (HS-s^z, Eq. SzHS)
+or in the charge channel (HS-n, Eq. DensityHS).
 
-Follows Sec. II.B (Eqs. SzHS, coupling, ConfgWeight, GrFMat and the
-implementation notes 'First'..'Fifth') and Sec. III.B (Eqs. DetailBalance,
-DRatio, GFupdate, rRatioLocal, GupdateLocal, DelayG0, DelayRatio, DelayRgenk,
-FinalDelay).  Propagators are dense: B_l = e^{gamma diag(s_l)} E with
-E = e^{-dtau H0} from a Taylor series (no FFT), so this module is independent of
-the momentum-space propagation of Sec. III.A that the CUDA path uses.
+Follows Sec. II.B (Eqs. SzHS, DensityHS, coupling, BIOpSz, BIOpnT,
+ConfgWeight, GrFMat and the implementation notes 'First'..'Fifth') and
+Sec. III.B (Eqs. DetailBalance, DRatio, GFupdate, rRatioLocal, GupdateLocal,
+DelayG0, DelayRatio, DelayRgenk, FinalDelay).  Propagators are dense:
+B_l = e^{lambda diag(s_l)} E with E = e^{-dtau H0} from a Taylor series (no
+FFT), so this module is independent of the momentum-space propagation of
+Sec. III.A that the CUDA path uses.  lambda is the coupling of Eq. coupling:
+gamma_s = arccosh(e^{dtau U/2}) (spin channel, real) or
+gamma_c = i arccos(e^{-dtau U/2}) (charge channel, imaginary).
 
 Readings of the paper fixed here (the paper is silent or ambiguous):
   * the simulated spin is up; after the partial particle-hole transform the
-    down-spin propagator is the complex conjugate of the up-spin one (equal to
-    it without a twist) and contributes the scalar e^{-gamma sum s}, so
-    W(X) ~ e^{-gamma sum s} |det(1 + B_M...B_1)|^2 and a single flip at (l, i)
-    has weight ratio R = e^{2 gamma s_i} |r|^2 with r = 1 + Delta (1 - G_ii),
-    Delta = e^{-2 gamma s_i} - 1 (real: the twist only enters the hopping);
+    down-spin propagator is the complex conjugate of the up-spin one
+    ('Fourth').  Spin channel: the transform leaves the scalar e^{-gamma sum s},
+    so W(X) ~ e^{-gamma sum s} |det(1 + B_M...B_1)|^2 and a single flip at
+    (l, i) has weight ratio R = e^{2 gamma s_i} |r|^2.  Charge channel: the
+    scalar e^{+gamma_c sum s} of the transform cancels the e^{-gamma_c sum s}
+    of p(x) (Eq. BIOpnT), so W(X) ~ |det(1 + B_M...B_1)|^2 and R = |r|^2.  In
+    both, r = 1 + Delta (1 - G_ii) with Delta = e^{-2 lambda s_i} - 1 (real for
+    the spin channel, a unit-circle point minus one for the charge channel);
   * a sweep is a forward pass l = 1..M (wrap into slice l, then propose every
     site i = 0..N-1 in ascending order) followed by a backward pass l = M..1
     (propose, then unwrap); accept iff u < R;
@@ -36,28 +43,43 @@ from . import rng as _rng
 class Model:
     """Static data: lattice, K, E = e^{-dtau K}, its inverse and half steps, gamma."""
 
-    def __init__(self, L, t=1.0, U=3.73, beta=3.0, dtau=0.1, theta=(0.0, 0.0)):
+    def __init__(self, L, t=1.0, U=3.73, beta=3.0, dtau=0.1, theta=(0.0, 0.0), hs_channel=0):
         self.lat = Honeycomb(L, t=t, theta=theta)
         self.N = self.lat.N
         self.M = int(round(beta / dtau))
         if abs(self.M * dtau - beta) > 1e-9:
             raise ValueError("beta must be a multiple of dtau")
+        if hs_channel not in (0, 1):
+            raise ValueError("hs_channel must be 0 (spin, Eq. SzHS) or 1 (charge, Eq. DensityHS)")
         self.t, self.U, self.beta, self.dtau = t, U, beta, dtau
+        self.hs_channel = hs_channel
         self.K = self.lat.hopping_matrix()
-        self.is_complex = np.iscomplexobj(self.K)
-        # Eq. coupling: gamma_s = arccosh(e^{dtau U / 2})
+        # Eq. coupling: gamma_s = arccosh(e^{dtau U / 2}), gamma_c = i arccos(e^{-dtau U / 2})
         self.gamma = np.arccosh(np.exp(dtau * U / 2.0))
+        self.alpha = np.arccos(np.exp(-dtau * U / 2.0))
+        self.lam = self.gamma if hs_channel == 0 else 1j * self.alpha
+        self.is_complex = np.iscomplexobj(self.K) or hs_channel == 1
         self.E = expm_taylor(-dtau * self.K)
         self.Einv = expm_taylor(dtau * self.K)
         self.Eh = expm_taylor(-0.5 * dtau * self.K)
         self.Ehinv = expm_taylor(0.5 * dtau * self.K)
 
-    # B_l = e^{H_I(x_l)} e^{-dtau H0}, H_I = gamma diag(s_l) for spin up (Eqs. BIOpSz, ConfgWeight)
+    # B_l = e^{H_I(x_l)} e^{-dtau H0}, H_I = lambda diag(s_l) for spin up (Eqs. BIOpSz, BIOpnT, ConfgWeight)
     def B(self, s_l):
-        return np.exp(self.gamma * s_l.astype(float))[:, None] * self.E
+        return np.exp(self.lam * s_l.astype(float))[:, None] * self.E
 
     def Binv(self, s_l):
-        return self.Einv * np.exp(-self.gamma * s_l.astype(float))[None, :]
+        return self.Einv * np.exp(-self.lam * s_l.astype(float))[None, :]
+
+    def flip_delta(self, s_i):
+        """Delta = e^{-2 lambda s_i} - 1 of flipping s_i (Eq. DRatio)."""
+        return np.exp(-2.0 * self.lam * s_i) - 1.0
+
+    def weight_factor(self, s_i):
+        """W(X')/W(X) = weight_factor * |r|^2 for a flip of s_i: e^{2 gamma s_i}
+        from the scalar the particle-hole transform leaves in the spin channel,
+        1 in the charge channel."""
+        return np.exp(2.0 * self.gamma * s_i) if self.hs_channel == 0 else 1.0
 
     def wrap(self, G, s_l):
         """G -> B_l G B_l^-1 (Sec. III.A, first paragraph)."""
@@ -82,15 +104,17 @@ class Model:
         return np.linalg.inv(np.eye(self.N) + R @ Lm)
 
     def log_weight(self, field):
-        """log W(X) up to a field-independent constant: -gamma sum s + 2 log|det(1 + B_M..B_1)|.
+        """log W(X) up to a field-independent constant: 2 log|det(1 + B_M..B_1)|,
+        plus -gamma sum s in the spin channel.
 
         W is the up-spin determinant times its complex conjugate (Sec. II.B
         'Fourth'), so it is never negative; the returned sign is that of the
-        real determinant (real path) or 1 (twisted path)."""
+        real determinant (real path) or 1 (complex path)."""
         sign, ld = np.linalg.slogdet(np.eye(self.N) + self.chain_product(field, 1, self.M))
         if self.is_complex:
             sign = 1.0 if abs(sign) > 0 else 0.0
-        return -self.gamma * float(field.sum()) + 2.0 * ld, sign
+        scalar = -self.gamma * float(field.sum()) if self.hs_channel == 0 else 0.0
+        return scalar + 2.0 * ld, sign
 
     # ---- stabilised chains -----------------------------------------------
     def udt_R(self, field, l, n_stab):
@@ -118,12 +142,13 @@ class Model:
 
 
 def local_ratio(model, G, i, s_i):
-    """Eq. rRatioLocal with the spin-channel Delta and the particle-hole weight factor.
+    """Eq. rRatioLocal with the channel's Delta and the particle-hole weight factor.
 
-    Returns (R, r, Delta): R = W(X')/W(X) = e^{2 gamma s_i} |r|^2."""
-    Delta = np.exp(-2.0 * model.gamma * s_i) - 1.0
+    Returns (R, r, Delta): R = W(X')/W(X) = e^{2 gamma s_i} |r|^2 (spin channel)
+    or |r|^2 (charge channel)."""
+    Delta = model.flip_delta(s_i)
     r = 1.0 + Delta * (1.0 - G[i, i])
-    return np.exp(2.0 * model.gamma * s_i) * (r * np.conj(r)).real, r, Delta
+    return model.weight_factor(s_i) * (r * np.conj(r)).real, r, Delta
 
 
 class Chain:
@@ -168,11 +193,11 @@ class Chain:
         X, Y, sites = [], [], []
         for i in range(N):
             sig = float(s[i])
-            Delta = np.exp(-2.0 * m.gamma * sig) - 1.0
+            Delta = m.flip_delta(sig)
             # Eq. DelayRatio: r = 1 + Delta {1 - G0_ii + sum_m x_m(i) y_m(i)}
             corr = sum(X[q][i] * Y[q][i] for q in range(len(X)))
             r = 1.0 + Delta * (1.0 - G0[i, i] + corr)
-            R = np.exp(2.0 * m.gamma * sig) * (r * np.conj(r)).real
+            R = m.weight_factor(sig) * (r * np.conj(r)).real
             u = _rng.uniform(self.key, _rng.proposal_counter(self.sweep_index, pas, l, i, m.M, N))
             self.proposed += 1
             if u < R:                               # Eq. DetailBalance

@@ -1,6 +1,7 @@
 """Exhaustive Hubbard-Stratonovich sum for tiny systems:
 <O> = sum_X W(X) O(X) / sum_X W(X)  (Eq. GSObsQMC) with the oracle's weight
-W(X) ~ e^{-gamma sum s} |det(1 + B_M...B_1)|^2 and the oracle's Wick measurement
+(Model.log_weight: e^{-gamma sum s} |det(1 + B_M...B_1)|^2 in the spin channel,
+|det(1 + B_M...B_1)|^2 in the charge channel) and the oracle's Wick measurement
 on G at slice 0."""
 import itertools
 import numpy as np
