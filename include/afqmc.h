@@ -30,15 +30,18 @@
  *     retrievable with afqmc_last_error(handle).  Numeric failures (NaN/Inf)
  *     and device-side wait timeouts return a status; nothing traps.
  *
- * Scope of this version: the spin-channel field (hs_channel = 0), one Markov
- * chain per handle, periodic (theta = 0: real G) or twisted (theta != 0:
- * complex G, Sec. III.C) boundaries; FP64, optionally with a split-TF32
- * tensor-core flush (precision = 1).
+ * Scope of this version: the spin-channel field (hs_channel = 0, Eq. SzHS) or
+ * the charge-channel field (hs_channel = 1, Eq. DensityHS), one Markov chain
+ * per handle, periodic (theta = 0) or twisted (theta != 0, Sec. III.C)
+ * boundaries; FP64, optionally with tensor-core products (precision bits).
  *
- * Complex G (twisted boundaries): every N x N matrix that crosses this
- * boundary (afqmc_get_G, afqmc_wrap_matrix, afqmc_update_slice) is complex,
- * row-major, interleaved (re, im): 2 N^2 doubles.  On the device it is held as
- * its real 2N x 2N embedding [[Re, -Im], [Im, Re]].
+ * Complex G (twisted boundaries, or the charge channel, whose propagator
+ * e^{i alpha diag(s)} e^{-dtau K} is complex): every N x N matrix that crosses
+ * this boundary (afqmc_get_G, afqmc_wrap_matrix, afqmc_update_slice,
+ * afqmc_force_slice) is complex, row-major, interleaved (re, im): 2 N^2
+ * doubles.  On the device it is held as its real 2N x 2N embedding
+ * [[Re, -Im], [Im, Re]].  Only the spin channel with periodic boundaries has a
+ * real G.
  */
 #ifndef AFQMC_H
 #define AFQMC_H
@@ -70,7 +73,11 @@ typedef struct {
     double beta, dtau;     /* M = beta/dtau must be an integer (|M dtau - beta| < 1e-9) */
     double theta1, theta2; /* twist (Eq. kpoints: k = ((l + theta)/L) b), each in [0, 1);
                               any nonzero value selects the complex path */
-    int32_t hs_channel;    /* 0 = spin channel HS-s^z (Eq. SzHS); only 0 supported */
+    int32_t hs_channel;    /* 0 = spin channel HS-s^z (Eq. SzHS): B_l = e^{gamma_s diag(s)} e^{-dtau K},
+                              flip ratio R = e^{2 gamma_s s} |r|^2.  1 = charge channel HS-n
+                              (Eq. DensityHS): B_l = e^{i alpha diag(s)} e^{-dtau K} with
+                              gamma_c = i alpha = i arccos(e^{-dtau U/2}) (Eq. coupling), R = |r|^2,
+                              complex G.  Block proposals (afqmc_block_sweep) need 0 and theta = 0 */
     int32_t n_delay;       /* delay rank n_d >= 1; 1 is the local Sherman-Morrison update */
     int32_t n_stab;        /* slices between QR recomputations of G; M % n_stab == 0 */
     int32_t precision;     /* bit mask; 0 = FP64 everywhere.  Bit 0: delayed-update flush
@@ -149,8 +156,10 @@ afqmc_status afqmc_get_field(afqmc_handle* h, int8_t* s_host);
 
 /* Run n_sweeps sweeps (Sec. III.A: a forward pass l = 1..M and a backward pass
  * l = M..1; in each slice every site i = 0..N-1 is proposed once, accepted iff
- * u < e^{2 gamma s_i} r^2 with r = 1 + Delta (1 - G_ii), using the delayed
- * update of rank n_delay; G recomputed every n_stab slices).  stats may be NULL. */
+ * u < R with R = e^{2 gamma s_i} |r|^2 (spin channel) or |r|^2 (charge channel),
+ * r = 1 + Delta (1 - G_ii), Delta = e^{-2 gamma s_i} - 1 (gamma = gamma_s or
+ * gamma_c), using the delayed update of rank n_delay; G recomputed every
+ * n_stab slices).  stats may be NULL. */
 afqmc_status afqmc_sweep(afqmc_handle* h, int32_t n_sweeps, afqmc_sweep_stats* stats);
 
 /* Measure the current G (the slice the chain is at: slice 0 between sweeps) now.
@@ -178,9 +187,9 @@ afqmc_status afqmc_update_slice(afqmc_handle* h, int32_t slice, int32_t pass,
                                 uint64_t sweep_index, double* G, int32_t* n_accepted);
 
 /* Weight ratio of flipping s[l-1][i] (Eqs. DRatio, rRatioLocal with the
- * particle-hole factor): out[0] = R = e^{2 gamma s} |r|^2, out[1] = Re r,
- * out[2] = Im r (0 with periodic boundaries), r = 1 + Delta (1 - G_ii), using G
- * at slice l recomputed from scratch. */
+ * particle-hole factor): out[0] = R = e^{2 gamma s} |r|^2 (spin channel) or
+ * |r|^2 (charge channel), out[1] = Re r, out[2] = Im r (0 when G is real),
+ * r = 1 + Delta (1 - G_ii), using G at slice l recomputed from scratch. */
 afqmc_status afqmc_det_ratio(afqmc_handle* h, int32_t slice, int32_t site, double out[3]);
 
 /* Time-displaced measurement of the current field (call between sweeps, the
@@ -347,7 +356,8 @@ afqmc_status afqmc_block_sweep(afqmc_handle* h, afqmc_net* net, afqmc_block_stat
 
 /* Slice update in forced mode (test hook): flip exactly the sites of slice l
  * with mask[i] != 0 (host, N int8) on a given G (host, N*N, in/out), updating
- * the handle's field; *logR = sum over the flips of log R = 2 gamma s + log r^2. */
+ * the handle's field; *logR = sum over the flips of log R = 2 gamma s + log |r|^2
+ * (spin channel) or log |r|^2 (charge channel). */
 afqmc_status afqmc_force_slice(afqmc_handle* h, int32_t slice, const int8_t* mask, double* G, double* logR);
 
 /* Message of the last failed network call on net (never NULL); net == NULL:

@@ -141,8 +141,13 @@ def _dptr(a):
 
 
 # ----------------------------------------------------------------- C names
-# handles of twisted (complex-G) chains: their G buffers are complex128
+# handles of complex-G chains (twisted boundaries or the charge-channel field):
+# their G buffers are complex128
 _COMPLEX = set()
+
+
+def _params_complex(p):
+    return p.theta1 != 0.0 or p.theta2 != 0.0 or p.hs_channel == 1
 
 
 def _is_complex(h):
@@ -157,7 +162,7 @@ def afqmc_create(params, stream=None):
     h = _H()
     code = _lib.afqmc_create(ctypes.byref(params), ctypes.c_void_p(stream or 0), ctypes.byref(h))
     _check(code, None)
-    if params.theta1 != 0.0 or params.theta2 != 0.0:
+    if _params_complex(params):
         _COMPLEX.add(ctypes.cast(h, ctypes.c_void_p).value)
     return h
 
@@ -290,7 +295,7 @@ def afqmc_batch_create(params_list):
     b = _H()
     _check_batch(_lib.afqmc_batch_create(arr, len(params_list), ctypes.byref(b)), None)
     for i, p in enumerate(params_list):
-        if p.theta1 != 0.0 or p.theta2 != 0.0:
+        if _params_complex(p):
             _COMPLEX.add(ctypes.cast(_lib.afqmc_batch_chain(b, i), ctypes.c_void_p).value)
     return b
 
@@ -474,11 +479,11 @@ def afqmc_last_error(h=None):
 
 
 def make_params(L, beta, dtau, U, n_delay, n_stab, t=1.0, seed=0, chain=0, measure=0, device=0, L2=None,
-                precision=0, theta=(0.0, 0.0), update_ctas=0):
+                precision=0, theta=(0.0, 0.0), update_ctas=0, hs_channel=0):
     return afqmc_params(L1=L, L2=L if L2 is None else L2, t=t, U=U, beta=beta, dtau=dtau,
                         theta1=float(theta[0]), theta2=float(theta[1]),
-                        hs_channel=0, n_delay=n_delay, n_stab=n_stab, precision=precision, measure=measure,
-                        chain=chain, device=device, update_ctas=update_ctas, seed=seed)
+                        hs_channel=hs_channel, n_delay=n_delay, n_stab=n_stab, precision=precision,
+                        measure=measure, chain=chain, device=device, update_ctas=update_ctas, seed=seed)
 
 
 class Batch:

@@ -56,13 +56,16 @@ enum Op { OP_E = 0, OP_EINV = 1, OP_EH = 2, OP_EHINV = 3 };
 struct afqmc_handle {
     afqmc_params p{};
     // Np = 2 Nc physical sites; N = dimension of the device matrices: Np, or 2 Np
-    // for twisted boundaries, where every complex N x N matrix is held as its
-    // real embedding [[Re, -Im], [Im, Re]] (cplx = 1)
+    // for twisted boundaries or the charge-channel field, where every complex
+    // N x N matrix is held as its real embedding [[Re, -Im], [Im, Re]] (cplx = 1)
     int N = 0, Np = 0, Nc = 0, L1 = 0, L2 = 0, M = 0, ns = 0, nc = 0, nd = 0, W = UPD_WMAX;
     int cplx = 0;
+    int charge = 0;                // 1: charge-channel field (Eq. DensityHS), B_l = e^{i alpha diag(s)} E
     BondPhases bond_ph{};          // e^{i Phi} of the three bonds (measurements)
     double gamma = 0.0, egp = 1.0, egm = 1.0;      // e^{gamma}, e^{-gamma}
+    double alpha = 0.0, ca = 1.0, sa = 0.0;        // charge channel: alpha = arccos(e^{-dtau U/2}), cos, sin
     double dl_p = 0.0, dl_m = 0.0, ef_p = 1.0, ef_m = 1.0;
+    double dli_p = 0.0, dli_m = 0.0;               // Im Delta (charge channel)
     uint64_t key = 0, sweep_index = 0;
     unsigned long long* d_sweep = nullptr;   // device copy of sweep_index (read by the slice kernel)
     cudaStream_t stream = nullptr;
@@ -249,9 +252,21 @@ void launch_rowop(afqmc_handle* h, const double* in, double* out, int nrows, Op 
 }
 
 DiagScale no_scale() { return DiagScale{nullptr, 1.0, 1.0}; }
-DiagScale vscale(afqmc_handle* h, int l, int sign) {   // e^{sign gamma s_l}
+// The diagonal factor of B_l.  Spin channel: e^{spin_sign gamma s_l} (real).
+// Charge channel: the complex factor e^{charge_sign i alpha s_l} by which the
+// row kernel multiplies the complex vectors of the embedding; each call site
+// states which one it needs (for a row of the embedding the kernel's vector is
+// the conjugate row, for a column it is the column itself).
+DiagScale vdiag(afqmc_handle* h, int l, int spin_sign, int charge_sign) {
     const int8_t* s = h->field + (size_t)(l - 1) * h->Np;
-    return sign > 0 ? DiagScale{s, h->egp, h->egm} : DiagScale{s, h->egm, h->egp};
+    if (h->charge) {
+        DiagScale d{s, h->ca, h->ca};
+        d.ip = charge_sign > 0 ? h->sa : -h->sa;      // s = +1: e^{+-i alpha}
+        d.im = -d.ip;                                  // s = -1: the conjugate
+        d.phase = 1;
+        return d;
+    }
+    return spin_sign > 0 ? DiagScale{s, h->egp, h->egm} : DiagScale{s, h->egm, h->egp};
 }
 
 // C = alpha rs .* (op(A) op(B)) .* cs + beta C on the BF16 tensor cores, FP64-accurate (ozaki.cuh)
@@ -351,10 +366,12 @@ void udt_extend(afqmc_handle* h, const UDTe& in, const UDTe& out, int lo, int hi
     const int n = h->N;
     double* A = h->Wk[0];
     CK(cudaMemcpyAsync(A, in.Ut, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, h->stream));
+    // rows of A = U^T are the columns of U: B U = V E U (left), B^+ U = E V^+ U (L chain,
+    // the real transpose of the embedding is the embedding of the adjoint)
     if (left) {
-        for (int l = lo; l <= hi; ++l) launch_rowop(h, A, A, n, OP_E, no_scale(), vscale(h, l, +1), false);
+        for (int l = lo; l <= hi; ++l) launch_rowop(h, A, A, n, OP_E, no_scale(), vdiag(h, l, +1, +1), false);
     } else {
-        for (int l = hi; l >= lo; --l) launch_rowop(h, A, A, n, OP_E, vscale(h, l, +1), no_scale(), false);
+        for (int l = hi; l >= lo; --l) launch_rowop(h, A, A, n, OP_E, vdiag(h, l, +1, -1), no_scale(), false);
     }
     // pre-pivoting by scaled column norms, unpivoted Householder QR of A P
     double* AP = h->Wk[1];
@@ -431,12 +448,14 @@ void set_identity(afqmc_handle* h, const UDTe& e) {
 void wrap(afqmc_handle* h, double* A, int l, int dir) {
     const int n = h->N;
     double* T = h->Wk[4];
+    // pass 1 right-multiplies the rows (A E^-1 V^-1, or A V E); pass 2 acts on the rows
+    // of the adjoint, i.e. left-multiplies (V E ., or E^-1 V^-1 .)
     if (dir > 0) {
-        launch_rowop(h, A, T, n, OP_EINV, no_scale(), vscale(h, l, -1), true);
-        launch_rowop(h, T, A, n, OP_E, no_scale(), vscale(h, l, +1), true);
+        launch_rowop(h, A, T, n, OP_EINV, no_scale(), vdiag(h, l, -1, +1), true);
+        launch_rowop(h, T, A, n, OP_E, no_scale(), vdiag(h, l, +1, +1), true);
     } else {
-        launch_rowop(h, A, T, n, OP_E, vscale(h, l, +1), no_scale(), true);
-        launch_rowop(h, T, A, n, OP_EINV, vscale(h, l, -1), no_scale(), true);
+        launch_rowop(h, A, T, n, OP_E, vdiag(h, l, +1, -1), no_scale(), true);
+        launch_rowop(h, T, A, n, OP_EINV, vdiag(h, l, -1, -1), no_scale(), true);
     }
 }
 
@@ -457,8 +476,9 @@ void update_slice(afqmc_handle* h, double* G, int l, int pass, int64_t sweep, co
     a.s = h->field + (size_t)(l - 1) * h->Np;
     a.nd = h->nd; a.W = h->W;
     a.pair = h->cplx; a.Np = h->Np;
-    a.force = force; a.logR = logR; a.two_gamma = 2.0 * h->gamma;
+    a.force = force; a.logR = logR; a.two_gamma = h->charge ? 0.0 : 2.0 * h->gamma;
     a.dl_p = h->dl_p; a.dl_m = h->dl_m; a.ef_p = h->ef_p; a.ef_m = h->ef_m;
+    a.charge = h->charge; a.dli_p = h->dli_p; a.dli_m = h->dli_m;
     a.key = h->key;
     a.ctr_stride = 2ull * (uint64_t)h->M * (uint64_t)h->Np;
     a.ctr0 = ((uint64_t)pass * (uint64_t)h->M + (uint64_t)(l - 1)) * (uint64_t)h->Np + 1;
@@ -665,8 +685,8 @@ void td_measure(afqmc_handle* h) {
                 k_transpose_scale<<<g, b, 0, h->stream>>>(h->td_t0, h->td_tmp, n, n, nullptr, 0, nullptr, 0);
             }
             CK(cudaGetLastError());
-            launch_rowop(h, h->td_tmp, h->td_t0, n, OP_E, no_scale(), vscale(h, l, +1), true);     // B_l G(tau, 0)
-            launch_rowop(h, h->td_0t, h->td_0t, n, OP_EINV, no_scale(), vscale(h, l, -1), false);  // G(0, tau) B_l^-1
+            launch_rowop(h, h->td_tmp, h->td_t0, n, OP_E, no_scale(), vdiag(h, l, +1, +1), true);     // B_l G(tau, 0)
+            launch_rowop(h, h->td_0t, h->td_0t, n, OP_EINV, no_scale(), vdiag(h, l, -1, +1), false);  // G(0, tau) B_l^-1
         }
         td_accumulate(h, l);
     }
@@ -739,7 +759,8 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
     if (!(P.U >= 0)) return bad("U must be >= 0");
     if (!(P.theta1 >= 0.0 && P.theta1 < 1.0 && P.theta2 >= 0.0 && P.theta2 < 1.0))
         return bad("twist angles theta1, theta2 must be in [0, 1)");
-    if (P.hs_channel != 0) return bad("only the spin channel (hs_channel = 0) is supported");
+    if (P.hs_channel != 0 && P.hs_channel != 1)
+        return bad("hs_channel must be 0 (spin channel, Eq. SzHS) or 1 (charge channel, Eq. DensityHS)");
     if (P.precision < 0 || P.precision > 3)
         return bad("precision must be 0..3 (bit 0: split-TF32 flush, bit 1: tensor-core FP64-accurate stabilisation products)");
     const double Mr = P.beta / P.dtau;
@@ -752,7 +773,8 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
     try {
         h->p = P;
         h->L1 = P.L1; h->L2 = P.L2; h->Nc = P.L1 * P.L2; h->Np = 2 * h->Nc; h->M = M;
-        h->cplx = (P.theta1 != 0.0 || P.theta2 != 0.0) ? 1 : 0;
+        h->charge = P.hs_channel == 1 ? 1 : 0;
+        h->cplx = (P.theta1 != 0.0 || P.theta2 != 0.0 || h->charge) ? 1 : 0;
         h->N = h->cplx ? 2 * h->Np : h->Np;
         h->ns = P.n_stab; h->nc = M / P.n_stab;
         // a physical flip is two rank-1 moves of the embedding when twisted
@@ -769,6 +791,16 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         h->egp = std::exp(h->gamma); h->egm = std::exp(-h->gamma);
         h->dl_p = std::exp(-2.0 * h->gamma) - 1.0;  h->dl_m = std::exp(2.0 * h->gamma) - 1.0;
         h->ef_p = std::exp(2.0 * h->gamma);         h->ef_m = std::exp(-2.0 * h->gamma);
+        if (h->charge) {
+            // Eq. coupling, charge channel: gamma_c = i alpha, alpha = arccos(e^{-dtau U/2});
+            // Delta = e^{-2 i alpha s} - 1, and the weight ratio is |r|^2 (no scalar factor)
+            h->alpha = std::acos(std::exp(-P.dtau * P.U / 2.0));
+            h->ca = std::cos(h->alpha); h->sa = std::sin(h->alpha);
+            const double c2 = std::cos(2.0 * h->alpha), s2 = std::sin(2.0 * h->alpha);
+            h->dl_p = c2 - 1.0; h->dli_p = -s2;
+            h->dl_m = c2 - 1.0; h->dli_m = s2;
+            h->ef_p = h->ef_m = 1.0;
+        }
         h->key = sm64_mix(P.seed ^ ((uint64_t)(P.chain + 1) * 0xD1B54A32D192ED03ull));
         CK(cudaSetDevice(P.device));
         CK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, P.device));
@@ -1080,7 +1112,7 @@ afqmc_status afqmc_det_ratio(afqmc_handle* h, int32_t slice, int32_t site, doubl
     CK(cudaStreamSynchronize(h->stream));
     double* o = h->vtmp;
     const GView gv{g, h->Np, h->N, h->cplx};
-    { Scope sc(h, AFQMC_K_MISC); k_ratio<<<1, 1, 0, h->stream>>>(gv, site, sv, h->dl_p, h->dl_m, h->ef_p, h->ef_m, o); }
+    { Scope sc(h, AFQMC_K_MISC); k_ratio<<<1, 1, 0, h->stream>>>(gv, site, sv, h->dl_p, h->dl_m, h->dli_p, h->dli_m, h->ef_p, h->ef_m, o); }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(out, o, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     return check_device(h);

@@ -197,11 +197,13 @@ __global__ void k_measure_scalars(GView g, const double* __restrict__ czz, const
 }
 
 // Weight ratio of flipping site i given G (test hook): out = {R, Re r, Im r},
-// R = e^{2 gamma s} |r|^2, r = 1 + Delta (1 - G_ii).
-__global__ void k_ratio(GView G, int i, int s, double dl_p, double dl_m, double ef_p, double ef_m, double* out) {
+// R = e^{2 gamma s} |r|^2 (spin channel) or |r|^2 (charge channel, ef = 1),
+// r = 1 + Delta (1 - G_ii) with Delta = dl + i dli.
+__global__ void k_ratio(GView G, int i, int s, double dl_p, double dl_m, double dli_p, double dli_m, double ef_p,
+                        double ef_m, double* out) {
     const double2 g = G.at(i, i);
-    const double dl = s > 0 ? dl_p : dl_m, ef = s > 0 ? ef_p : ef_m;
-    const double rr = fma(dl, 1.0 - g.x, 1.0), ri = -dl * g.y;
+    const double dl = s > 0 ? dl_p : dl_m, di = s > 0 ? dli_p : dli_m, ef = s > 0 ? ef_p : ef_m;
+    const double rr = fma(di, g.y, fma(dl, 1.0 - g.x, 1.0)), ri = fma(di, 1.0 - g.x, -dl * g.y);
     out[0] = ef * fma(rr, rr, ri * ri);
     out[1] = rr;
     out[2] = ri;

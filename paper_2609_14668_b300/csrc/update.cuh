@@ -8,6 +8,15 @@
 // Eq. DelayRgenk; after n_delay accepted moves, and at the end of the slice,
 // G <- G - X Y (Eq. FinalDelay).
 //
+// Charge channel (Eq. DensityHS, charge = 1, always on the embedding): Delta =
+// e^{-2 i alpha s_i} - 1 is complex and R = |r|^2.  The complex rank-1 move
+// G <- G - kappa G(:,p) (1 - G)(p,:), kappa = Delta / r, is in the embedding the
+// sum of two real rank-1 moves taken together (not one after the other):
+//   x1 = kappa_r z_p + kappa_i z_q,  x2 = -kappa_i z_p + kappa_r z_q,  y1 = w_p, y2 = w_q,
+// with z_p, z_q the columns p, q = p + Np and w_p, w_q the rows p, q of the
+// current G and 1 - G, so the window, the x/y recursion and the flush keep
+// their real form; mcoef holds kappa_r at the first and kappa_i at the second.
+//
 // GPU schedule (one cooperative kernel per slice, all SMs):
 //   B  CTA 0 proposes the sites of a window of W consecutive sites.  It holds
 //      the W x W block of the current G on chip and keeps it current with the
@@ -53,6 +62,8 @@ struct UpdArgs {
     const int8_t* force;
     double* logR;
     double two_gamma;
+    int charge;                   // 1: charge-channel field (complex Delta, pair mode)
+    double dli_p, dli_m;          // Im Delta for s = +1, -1 (charge channel)
 };
 
 // Window of the proposals.  Plain: positions t = 0..nw-1 are the sites c0 + t.
@@ -288,10 +299,10 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
             double* Gw = upd_smem;                        // W x (W+1)
             double* vv = Gw + W * (W + 1);                // W thresholds on r^2: u e^{-2 gamma s}
             double* dd = vv + W;                          // W values of Delta
-            double* od = dd + W;                          // W values of 1 + Delta
+            double* od = dd + W;                          // W values of 1 + Delta (charge: Im Delta)
             int8_t* sw = reinterpret_cast<int8_t*>(od + W); // W field values
             __shared__ int s_found[2];
-            __shared__ double s_c[2];
+            __shared__ double s_c[2], s_c2[2];
             const int nw = win_len(a, cursor);
             const int ld = W + 1;
             for (int o = threadIdx.x; o < nw * nw; o += blockDim.x) {
@@ -311,7 +322,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                     vv[t] = u * (sg > 0 ? a.ef_m : a.ef_p);
                 }
                 dd[t] = sg > 0 ? a.dl_p : a.dl_m;
-                od[t] = 1.0 + dd[t];
+                od[t] = a.charge ? (sg > 0 ? a.dli_p : a.dli_m) : 1.0 + dd[t];
                 sw[t] = (int8_t)sg;
             }
             __syncthreads();
@@ -321,9 +332,30 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                 const int slot = it & 1;
                 if (threadIdx.x == 0) {
                     int found = -1;
-                    double c = 0.0;
+                    double c = 0.0, c2 = 0.0;
                     for (; t0 < nw; ++t0) {
                         const double dl = dd[t0];
+                        if (a.charge) {
+                            // one complex flip per pair (t0 even): G_pp = Gw[t0][t0] + i Gw[t0+1][t0],
+                            // r = 1 + Delta (1 - G_pp), R = |r|^2, kappa = Delta conj(r) / |r|^2
+                            const double di = od[t0];
+                            const double gr = Gw[t0 * ld + t0], gi = Gw[(t0 + 1) * ld + t0];
+                            const double omg = 1.0 - gr;
+                            const double rr = fma(dl, omg, fma(di, gi, 1.0));
+                            const double ri = fma(di, omg, -dl * gi);
+                            const double R2 = fma(rr, rr, ri * ri);
+                            if (!isfinite(R2)) { flag_error(a.st, DERR_NUMERIC, 201); ++t0; continue; }
+                            if (R2 > vv[t0]) {
+                                const double inv = 1.0 / R2;
+                                found = t0;
+                                c = fma(dl, rr, di * ri) * inv;
+                                c2 = fma(di, rr, -dl * ri) * inv;
+                                if (a.force) lacc += log(R2);
+                                break;
+                            }
+                            ++t0;                    // rejected: skip the partner too
+                            continue;
+                        }
                         const double r = fma(-dl, Gw[t0 * ld + t0], od[t0]);   // 1 + Delta (1 - G_ii)
                         if (!isfinite(r)) { flag_error(a.st, DERR_NUMERIC, 200); continue; }
                         if (a.pair) {
@@ -355,14 +387,64 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                             break;
                         }
                     }
-                    if (found >= 0) ++t0;
+                    if (found >= 0) t0 += a.charge ? 2 : 1;
                     s_found[slot] = found;
                     s_c[slot] = c;
+                    s_c2[slot] = c2;
                 }
                 __syncthreads();
                 const int tf = s_found[slot];
                 if (tf < 0) break;
                 const double c = s_c[slot];
+                if (a.charge) {
+                    // the pair (tf, tg) as two simultaneous real moves (x1, y1), (x2, y2)
+                    const double c2 = s_c2[slot];
+                    const int tg = tf + 1;
+                    if (threadIdx.x == 32) {
+                        a.msite[kk] = win_site(a, cursor, tf);
+                        a.msite[kk + 1] = win_site(a, cursor, tg);
+                        a.mcoef[kk] = c;
+                        a.mcoef[kk + 1] = c2;
+                        a.s[win_phys(a, cursor, tf)] = (int8_t)(-sw[tf]);
+                    }
+                    const int rest = nw - tg - 1;
+                    for (int p = (int)threadIdx.x - 32; p >= 0 && p < rest; p += blockDim.x - 32) {
+                        const int q = tg + 1 + p;
+                        const double zp = Gw[q * ld + tf], zq = Gw[q * ld + tg];
+                        a.xw[kk * W + q] = fma(c, zp, c2 * zq);
+                        a.xw[(kk + 1) * W + q] = fma(-c2, zp, c * zq);
+                        a.yw[kk * W + q] = -Gw[tf * ld + q];
+                        a.yw[(kk + 1) * W + q] = -Gw[tg * ld + q];
+                    }
+                    if (threadIdx.x < 32) {
+                        // warp 0: the diagonal and the two entries inside each later pair
+                        const int q = tg + 1 + (int)threadIdx.x;
+                        if (q < nw) {
+                            const double x1 = fma(c, Gw[q * ld + tf], c2 * Gw[q * ld + tg]);
+                            const double x2 = fma(-c2, Gw[q * ld + tf], c * Gw[q * ld + tg]);
+                            Gw[q * ld + q] = fma(x1, Gw[tf * ld + q], fma(x2, Gw[tg * ld + q], Gw[q * ld + q]));
+                            if (!(q & 1) && q + 1 < nw) {
+                                const int q1 = q + 1;
+                                const double v1 = fma(c, Gw[q1 * ld + tf], c2 * Gw[q1 * ld + tg]);
+                                const double v2 = fma(-c2, Gw[q1 * ld + tf], c * Gw[q1 * ld + tg]);
+                                Gw[q1 * ld + q] = fma(v1, Gw[tf * ld + q], fma(v2, Gw[tg * ld + q], Gw[q1 * ld + q]));
+                                Gw[q * ld + q1] = fma(x1, Gw[tf * ld + q1], fma(x2, Gw[tg * ld + q1], Gw[q * ld + q1]));
+                            }
+                        }
+                        __syncwarp();
+                    } else {
+                        for (int o = threadIdx.x - 32; o < rest * rest; o += blockDim.x - 32) {
+                            const int q = tg + 1 + o / rest, pp = tg + 1 + o % rest;
+                            if ((q >> 1) == (pp >> 1)) continue;      // warp 0's entries
+                            const double x1 = fma(c, Gw[q * ld + tf], c2 * Gw[q * ld + tg]);
+                            const double x2 = fma(-c2, Gw[q * ld + tf], c * Gw[q * ld + tg]);
+                            Gw[q * ld + pp] = fma(x1, Gw[tf * ld + pp], fma(x2, Gw[tg * ld + pp], Gw[q * ld + pp]));
+                        }
+                    }
+                    kk += 2;
+                    if (kk >= nd) { tstop = tg + 1; break; }
+                    continue;
+                }
                 if (threadIdx.x == 32) {
                     a.msite[kk] = win_site(a, cursor, tf);
                     a.mcoef[kk] = c;
@@ -492,7 +574,23 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                 double ax = mine ? g_jm - (ox0 + ox1) : 0.0;
                 double ay = mine ? (j == im ? 1.0 : 0.0) - g_mj + (oy0 + oy1) : 0.0;
                 double xv = 0.0, yv = 0.0;
-                for (int q = 0; q < nn; ++q) {
+                if (a.charge) {
+                    // moves come in pairs (q, q + 1) of one complex flip: both take the
+                    // columns and rows as they were before the pair, x mixes them by kappa
+                    for (int q = 0; q + 1 < nn; q += 2) {
+                        const double axa = __shfl_sync(0xffffffffu, ax, q), axb = __shfl_sync(0xffffffffu, ax, q + 1);
+                        const double kr = __shfl_sync(0xffffffffu, cm, q), ki = __shfl_sync(0xffffffffu, cm, q + 1);
+                        if (lane == q) { xv = fma(kr, axa, ki * axb); yv = ay; }
+                        if (lane == q + 1) { xv = fma(-ki, axa, kr * axb); yv = ay; }
+                        const double x0 = __shfl_sync(0xffffffffu, xv, q), y0 = __shfl_sync(0xffffffffu, yv, q);
+                        const double x1 = __shfl_sync(0xffffffffu, xv, q + 1), y1 = __shfl_sync(0xffffffffu, yv, q + 1);
+                        if (mine && lane > q + 1) {
+                            ax = fma(-x0, syw[q * W + tm], fma(-x1, syw[(q + 1) * W + tm], ax));
+                            ay = fma(sxw[q * W + tm], y0, fma(sxw[(q + 1) * W + tm], y1, ay));
+                        }
+                    }
+                }
+                for (int q = 0; q < nn && !a.charge; ++q) {
                     if (lane == q) { xv = cm * ax; yv = ay; }
                     const double xq = __shfl_sync(0xffffffffu, xv, q);
                     const double yq = __shfl_sync(0xffffffffu, yv, q);

@@ -28,11 +28,19 @@ struct FFTPlan {
     const double2* tw2;                   // e^{-2 pi i m / L2}, m < L2
 };
 
-// Diagonal scaling d_i = s_i > 0 ? vp : vm, or 1 when s == nullptr.
+// Diagonal scaling d_i = s_i > 0 ? vp : vm, or 1 when s == nullptr.  With
+// phase != 0 (charge-channel field, complex operator path only) the factor is
+// the complex number (vp, ip) or (vm, im) that multiplies each complex vector
+// element of the embedding rows (see k_rowop).
 struct DiagScale {
     const int8_t* s;
     double vp, vm;
+    double ip = 0.0, im = 0.0;
+    int phase = 0;
     __device__ __forceinline__ double at(int i) const { return s ? (s[i] > 0 ? vp : vm) : 1.0; }
+    __device__ __forceinline__ double2 cat(int i) const {
+        return s ? (s[i] > 0 ? make_double2(vp, ip) : make_double2(vm, im)) : make_double2(1.0, 0.0);
+    }
 };
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
@@ -149,7 +157,9 @@ __device__ double2* dft2d(double2* z, double2* t, int VP, const FFTPlan& P, bool
 // writes [Re Op z, Im Op z].  For a column of the embedding this is the
 // embedding of Op applied to the complex column; for a row it is the row
 // times the embedding of Op, because every Op used here (e^{+-c dtau K}) is
-// Hermitian.  The diagonal scalings act on both halves.
+// Hermitian.  The diagonal scalings act on both halves; a complex scaling
+// (DiagScale::phase) multiplies z itself, so for a row z = conj(row) a factor
+// c applies conj(c) to the row, and for a column it applies c.
 __global__ void __launch_bounds__(256) k_rowop(const double* in, double* out,
                                                int nrows, int ldi, int ldo, FFTPlan P,
                                                const double2* __restrict__ blk,
@@ -166,7 +176,9 @@ __global__ void __launch_bounds__(256) k_rowop(const double* in, double* out,
         if (emb) {
             const int r = r0 + v;
             const double* row = in + (size_t)r * ldi;
-            z[o] = r < nrows ? make_double2(row[j] * d, row[N + j] * d) : make_double2(0.0, 0.0);
+            if (r >= nrows) { z[o] = make_double2(0.0, 0.0); continue; }
+            z[o] = pre.phase ? cmul(make_double2(row[j], row[N + j]), pre.cat(j))
+                             : make_double2(row[j] * d, row[N + j] * d);
             continue;
         }
         const int ra = r0 + 2 * v, rb = ra + 1;
@@ -195,6 +207,12 @@ __global__ void __launch_bounds__(256) k_rowop(const double* in, double* out,
                 const int v = o / N, j = o - v * N;
                 const int r = r0 + v;
                 if (r >= nrows) continue;
+                if (post.phase) {
+                    const double2 q = cmul(res[o], post.cat(j));
+                    out[(size_t)r * ldo + j] = q.x * inv;
+                    out[(size_t)r * ldo + N + j] = q.y * inv;
+                    continue;
+                }
                 const double d = post.at(j) * inv;
                 const double2 q = res[o];
                 out[(size_t)r * ldo + j] = q.x * d;
@@ -207,6 +225,11 @@ __global__ void __launch_bounds__(256) k_rowop(const double* in, double* out,
                 if (r >= nrows) continue;
                 const int j = j2 < N ? j2 : j2 - N;
                 const double2 q = res[(size_t)v * N + j];
+                if (post.phase) {
+                    const double2 qc = cmul(q, post.cat(j));
+                    out[(size_t)j2 * ldo + r] = (j2 < N ? qc.x : qc.y) * inv;
+                    continue;
+                }
                 out[(size_t)j2 * ldo + r] = (j2 < N ? q.x : q.y) * post.at(j) * inv;
             }
         }
