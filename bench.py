@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD_KEY, choices=sorted(WORKLOADS) + ["batched", "learned"],
                     help="batched: 64 chains, L in {6, 9, 12}, 16 twists each, one graph per batched sweep")
     ap.add_argument("--no-autotune", action="store_true", help="batched: skip the autotuner (n_delay 16, all SMs)")
+    ap.add_argument("--twists", choices=["grid", "quasirandom"], default="grid",
+                    help="batched: the uniform 4x4 twist grid, or the first 16 points of the library's "
+                         "quasi-random (Halton 2,3) twist sequence")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tau-sweeps", type=int, default=15,
@@ -88,7 +91,8 @@ def oracle_sample(key, seed=11):
     from oracle.linalg import udt_left_multiply, stable_green
     w, N, M = workload_config(key)
     ns = w["n_stab"]
-    m = Model(w["L"], U=w["U"], beta=2 * ns * w["dtau"], dtau=w["dtau"])     # same N and B_l, 2 n_stab slices
+    m = Model(w["L"], U=w["U"], beta=2 * ns * w["dtau"], dtau=w["dtau"],
+              hs_channel=w.get("hs_channel", 0))                            # same N and B_l, 2 n_stab slices
     f = random_field(m.M, m.N, seed)
     ch = Chain(m, n_delay=w["n_delay"], n_stab=ns, seed=seed, field=f)
     t0 = time.perf_counter()
@@ -163,7 +167,7 @@ def run_reference(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": key, "L": w["L"], "N_sites": N, "beta": w["beta"], "dtau": w["dtau"], "M": M,
                       "U": w["U"], "n_delay": w["n_delay"], "n_stab": w["n_stab"], "precision": 0,
-                      "parallelism": "host cores (numpy/BLAS threads)"},
+                      "hs_channel": w.get("hs_channel", 0), "parallelism": "host cores (numpy/BLAS threads)"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
                             "sample": (f"each step: one wrap + one slice update ({N} proposals) + one "
                                        f"stabilisation of the FP64 numpy oracle; value = N / (t_slice + "
@@ -227,20 +231,26 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- roofline
-def algorithmic_flops(family, N, Nc, accepted_per_update):
-    """Algorithmic FP64 flops of one launch of each kernel family (all matrices N x N)."""
+def algorithmic_flops(family, N, Nc, accepted_per_update, cplx=False):
+    """Algorithmic FP64 flops of one launch of each kernel family (all matrices N x N,
+    N physical sites).  cplx: complex matrices (charge channel), counted as complex
+    arithmetic (a complex multiply-add is 4 real ones); the device's real 2N x 2N
+    embedding does twice that work, which shows as a lower fraction."""
     import math
+    c = 4.0 if cplx else 1.0
     if family == "gemm":
-        return 2.0 * N ** 3
+        return c * 2.0 * N ** 3
     if family == "qr":
-        return 4.0 * N ** 3 / 3.0                       # Householder QR, square
+        return c * 4.0 * N ** 3 / 3.0                   # Householder QR, square
     if family == "lu":
-        return 2.0 * N ** 3 / 3.0                       # LU with partial pivoting, square
+        return c * 2.0 * N ** 3 / 3.0                   # LU with partial pivoting, square
     if family == "update":
-        return 2.0 * N * N * accepted_per_update        # Eq. FinalDelay: 2 N^2 per accepted flip
+        return c * 2.0 * N * N * accepted_per_update    # Eq. FinalDelay: 2 N^2 per accepted flip
     if family == "propagate":
-        # N/2 complex row pairs, each: 4 complex FFTs of size Nc (5 n log2 n) + 2x2 block per k (32 flops)
-        return (N / 2.0) * (4 * 5.0 * Nc * math.log2(max(Nc, 2)) + 32.0 * Nc)
+        # real: N/2 complex row pairs; complex: N complex rows.  Each: 4 complex FFTs of
+        # size Nc (5 n log2 n) + 2x2 block per k (32 flops)
+        rows = N if cplx else N / 2.0
+        return rows * (4 * 5.0 * Nc * math.log2(max(Nc, 2)) + 32.0 * Nc)
     return None
 
 
@@ -283,7 +293,8 @@ def time_chain(pkg, torch, args, key, precision, rank, world, dev, dist, stream)
     for c in range(C):
         params = pkg.make_params(L=w["L"], beta=w["beta"], dtau=w["dtau"], U=w["U"], n_delay=w["n_delay"],
                                  n_stab=w["n_stab"], seed=seed, chain=idx[c], measure=1,
-                                 device=dev, precision=precision, update_ctas=args.update_ctas)
+                                 device=dev, precision=precision, update_ctas=args.update_ctas,
+                                 hs_channel=w.get("hs_channel", 0))
         chains.append(pkg.Chain(params, stream=streams[c].cuda_stream))
     ch = chains[0]
 
@@ -391,7 +402,7 @@ def captured_traffic(fam, precision, N):
     return nbytes
 
 
-def roofline_of(res, N, precision):
+def roofline_of(res, N, precision, cplx=False):
     """Roofline of the dominant kernel family: its algorithmic work per launch over
     its average launch duration, timed with events in the timed region."""
     timing, breakdown, fam, accepted = res["timing"], res["breakdown"], res["dominant"], res["accepted"]
@@ -399,21 +410,22 @@ def roofline_of(res, N, precision):
     nl, tms = timing[fam]
     acc_per_update = accepted / max(timing["update"][0], 1)
     if fam == "update" and (precision & 1):
-        # flush on the tensor cores: 2 N^2 algorithmic flops per accepted flip, each
-        # product done as three TF32 products (split-TF32), so the peak is TF32 / 3
-        fl = 2.0 * N * N * acc_per_update
+        # flush on the tensor cores: 2 N^2 algorithmic flops per accepted flip (x 4 for
+        # complex G), each product done as three TF32 products (split-TF32), so the
+        # peak is TF32 / 3
+        fl = (4.0 if cplx else 1.0) * 2.0 * N * N * acc_per_update
         peak, bound, unit = TF32_PEAK_TFLOPS / 3.0, "tensor", "TFLOP/s"
         note = ("split-TF32 peak = TF32 dense / 3; TF32 dense = measured BF16 burst x nominal "
                 "TF32/BF16 ratio (1.1/2.25)")
     else:
-        fl = algorithmic_flops(fam, N, Nc, acc_per_update)
+        fl = algorithmic_flops(fam, N, Nc, acc_per_update, cplx)
         peak, bound, unit = FP64_PEAK_TFLOPS, "alu", "TFLOP/s"
         note = "nominal B300 FP64 (DFMA microbenchmark on this pool: 1.13 TFLOP/s)"
     if fl is None:
         return None
     ach = fl / (tms / nl / 1e3) / 1e12
     return {"bound": bound, "kernel": fam, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-            "traffic": captured_traffic(fam, precision, N), "peak_note": note, "flops_per_launch": fl, "avg_launch_ms": tms / nl,
+            "traffic": None if cplx else captured_traffic(fam, precision, N), "peak_note": note, "flops_per_launch": fl, "avg_launch_ms": tms / nl,
             "share_of_step": breakdown[fam][1] / sum(v[1] for v in breakdown.values()),
             "share_note": "share of device time in one breakdown sweep per chain with every launch timed"}
 
@@ -432,6 +444,7 @@ def run_ours(args):
     dev = local if world > 1 else 0
     key = args.workload
     w, N, M = workload_config(key)
+    cplx = w.get("hs_channel", 0) == 1
     stream = torch.cuda.Stream(device=dev)
     # headline: the reduced-precision workload (split-TF32 flush); then the plain FP64 sweep
     head = time_chain(pkg, torch, args, key, args.precision, rank, world, dev, dist, stream)
@@ -502,10 +515,11 @@ def run_ours(args):
            "data": "synthetic (random initial Ising field from the seed; no dataset)",
            "config": {"workload": key, "L": w["L"], "N_sites": N, "beta": w["beta"], "dtau": w["dtau"], "M": M,
                       "U": w["U"], "n_delay": w["n_delay"], "n_stab": w["n_stab"], "precision": args.precision,
+                      "hs_channel": w.get("hs_channel", 0),
                       "chains_per_gpu": max(1, args.chains), "update_ctas": args.update_ctas or "one per SM",
                       "parallelism": f"replicas{world}",
                       "l2": "no flush: a sweep streams the UDT stacks (1.3 GB) through the 126 MB L2"},
-           "roofline": roofline_of(head, N, args.precision),
+           "roofline": roofline_of(head, N, args.precision, cplx),
            "gpu_launches": int(head["launches"]),
            "acceptance": head["accepted"] / max(head["proposed"], 1), "max_stab_drift": head["drift"],
            "kernel_ms_breakdown_sweep": {k: {"launches": v[0], "ms": v[1]} for k, v in head["breakdown"].items()},
@@ -518,7 +532,7 @@ def run_ours(args):
                        "obs_rel_diff_vs_fp64": rel,
                        "kernel_ms_breakdown_sweep": {k: {"launches": v[0], "ms": v[1]}
                                                      for k, v in ref64["breakdown"].items()},
-                       "roofline": roofline_of(ref64, N, 0)}
+                       "roofline": roofline_of(ref64, N, 0, cplx)}
     if e2e:
         out["e2e"] = e2e
     if autocorr:
@@ -552,7 +566,8 @@ def run_batched(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group(backend="nccl")
-    spec = batched_chains()
+    twist_list = pkg.afqmc_quasirandom_twists(BATCHED["twists"] ** 2, 1) if args.twists == "quasirandom" else None
+    spec = batched_chains(twist_list)
 
     def params(i, L, beta, th, nd, ct):
         return pkg.make_params(L=L, beta=beta, dtau=BATCHED["dtau"], U=BATCHED["U"], n_delay=nd,
@@ -610,7 +625,9 @@ def run_batched(args):
            "ms_per_step": wall * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (random initial Ising fields; no dataset)",
            "config": {"workload": "batched", "chains": len(spec), "sizes": [list(x) for x in BATCHED["sizes"]],
-                      "twist_grid": f"{BATCHED['twists']}x{BATCHED['twists']}", "dtau": BATCHED["dtau"],
+                      "twist_grid": (f"{BATCHED['twists']}x{BATCHED['twists']}" if args.twists == "grid" else
+                                     f"quasi-random: Halton (2, 3) points 1..{BATCHED['twists'] ** 2}"),
+                      "dtau": BATCHED["dtau"],
                       "U": BATCHED["U"], "n_stab": BATCHED["n_stab"], "beta": "t*beta = L",
                       "l2": "no flush: 64 chains' stacks (~0.9 GB) exceed the 126 MB L2",
                       "timing": "host wall clock around the batched sweeps, synchronised on both sides "

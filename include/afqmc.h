@@ -364,6 +364,19 @@ afqmc_status afqmc_force_slice(afqmc_handle* h, int32_t slice, const int8_t* mas
  * the last failure of afqmc_net_create on this thread. */
 const char* afqmc_net_last_error(const afqmc_net* net);
 
+/* Twist angles for twist-averaged boundary conditions (Sec. III.C: N_Theta
+ * independent twisted chains whose observables are averaged, the (theta1,
+ * theta2) drawn from a 2D quasi-random sequence with the cumulative property).
+ * The paper does not name the sequence; this library uses the Halton sequence
+ * in bases 2 and 3: theta[2i] = phi_2(start + i), theta[2i+1] = phi_3(start + i),
+ * phi_b the radical inverse (base-b digits mirrored behind the point), exact
+ * fractions rounded once to double, each in [0, 1).  start = 1 skips the
+ * periodic point (0, 0).  Any prefix of the sequence is evenly spread, so
+ * N_Theta can grow without discarding chains.  theta: host, 2n doubles.
+ * Host-only (no device work); AFQMC_E_INVALID if n < 0, start < 0 or
+ * start + n >= 2^31, message in afqmc_last_error(NULL). */
+afqmc_status afqmc_quasirandom_twists(int32_t n, int32_t start, double* theta);
+
 /* Sizes of the handle: N (physical sites 2 Nc), M, Nc. */
 afqmc_status afqmc_dims(const afqmc_handle* h, int32_t* N, int32_t* M, int32_t* Nc);
 

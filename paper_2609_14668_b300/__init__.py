@@ -105,6 +105,7 @@ _SIGS = {
     "afqmc_force_slice": ([_H, ctypes.c_int32, _I8P, _DP, _DP]),
     "afqmc_measure_td": ([_H]),
     "afqmc_get_td": ([_H, _DP, _DP, _DP, _P(ctypes.c_int64)]),
+    "afqmc_quasirandom_twists": ([ctypes.c_int32, ctypes.c_int32, _DP]),
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -416,6 +417,14 @@ def afqmc_block_sweep(h, net):
     st = afqmc_block_stats()
     _check(_lib.afqmc_block_sweep(h, net, ctypes.byref(st)), h)
     return st
+
+
+def afqmc_quasirandom_twists(n, start=1):
+    """(n, 2) array of twist angles (theta1, theta2): the 2D Halton sequence in
+    bases 2 and 3 from index start (host-only)."""
+    out = np.zeros((max(n, 0), 2))
+    _check(_lib.afqmc_quasirandom_twists(n, start, _dptr(out) if n > 0 else None), None)
+    return out
 
 
 def afqmc_measure_td(h):

@@ -1871,4 +1871,28 @@ const char* afqmc_last_error(const afqmc_handle* h) {
     return h->err.c_str();
 }
 
+// Radical inverse of n in base b as the exact fraction r / b^k (digits of n
+// reversed behind the point), converted by one correctly rounded division.
+static double radical_inverse(uint64_t n, uint64_t b) {
+    uint64_t r = 0, d = 1;
+    for (; n; n /= b) {
+        r = r * b + n % b;
+        d *= b;
+    }
+    return (double)r / (double)d;
+}
+
+afqmc_status afqmc_quasirandom_twists(int32_t n, int32_t start, double* theta) {
+    if (n < 0 || start < 0 || (int64_t)start + n > 2147483647ll || (n > 0 && !theta)) {
+        g_create_error = "afqmc_quasirandom_twists: need n >= 0, start >= 0, start + n < 2^31 and a buffer";
+        return AFQMC_E_INVALID;
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        const uint64_t m = (uint64_t)start + (uint64_t)i;
+        theta[2 * i] = radical_inverse(m, 2);
+        theta[2 * i + 1] = radical_inverse(m, 3);
+    }
+    return AFQMC_OK;
+}
+
 }  // extern "C"

@@ -8,8 +8,9 @@ consume these inputs; neither side's numerics live here.
 """
 import numpy as np
 
-# The five workload configurations (honeycomb Hubbard model, t = 1, half filling,
-# periodic boundaries, spin-channel Ising Hubbard-Stratonovich field).
+# Workload configurations (honeycomb Hubbard model, t = 1, half filling,
+# periodic boundaries; spin-channel Ising Hubbard-Stratonovich field unless
+# hs_channel = 1, the charge channel).
 WORKLOADS = {
     # small case the oracle finishes in seconds
     "L3_beta3": dict(L=3, beta=3.0, dtau=0.1, U=3.73, n_delay=4, n_stab=10),
@@ -20,6 +21,9 @@ WORKLOADS = {
     # same N and kernels as the headline workload, 16 slices: small device
     # footprint for profiler captures
     "L24_beta1.6": dict(L=24, beta=1.6, dtau=0.1, U=3.73, n_delay=64, n_stab=8),
+    # the headline shape with the charge-channel field (complex G, hs_channel = 1)
+    "L24_beta24_charge": dict(L=24, beta=24.0, dtau=0.1, U=3.73, n_delay=64, n_stab=8, hs_channel=1),
+    "L24_beta1.6_charge": dict(L=24, beta=1.6, dtau=0.1, U=3.73, n_delay=64, n_stab=8, hs_channel=1),
 }
 
 
@@ -38,15 +42,20 @@ LEARNED = dict(L=6, beta=6.0, dtau=0.1, U=3.73, n_delay=32, n_stab=10, b=2, T=2,
                n_cfg=600, train_steps=2000, batch=256, lr=3e-3)
 
 
-def batched_chains():
-    """(L, beta, theta, replica) of every chain of the batched workload."""
+def batched_chains(twists=None):
+    """(L, beta, theta, replica) of every chain of the batched workload.  twists:
+    an explicit list of g*g twist angle pairs (e.g. a quasi-random sequence)
+    replacing the uniform g x g grid."""
     out = []
     g = BATCHED["twists"]
+    grid = [(a / g, b / g) for a in range(g) for b in range(g)] if twists is None else \
+        [(float(t[0]), float(t[1])) for t in twists]
+    if len(grid) != g * g:
+        raise ValueError(f"the batched workload takes {g * g} twists per size")
     for L, reps in BATCHED["sizes"]:
-        for a in range(g):
-            for b in range(g):
-                for r in range(reps):
-                    out.append((L, float(L), (a / g, b / g), r))
+        for th in grid:
+            for r in range(reps):
+                out.append((L, float(L), th, r))
     return out
 
 
