@@ -379,11 +379,11 @@ def time_chain(pkg, torch, args, key, precision, rank, world, dev, dist, stream)
 # (profiles/k_update_slice_L24.md: same N and n_delay as the L=24 workload).
 CAPTURED_TRAFFIC = {
     ("update", 1, 1152): ("paper_2609_14668_b300/csrc/update.cuh",
-                          "d3929de7e731b841b1a169c13348f06eff6e9aaf9c794d93243a4fff4cb4c0bd",
-                          10.734848e6 + 0.096256e6),
+                          "c76ababa5c8e37f55e01ef2871eed5f0b40d437a81dd075e09282893bed3c9a3",
+                          10.744832e6 + 0.117760e6),
     ("update", 3, 1152): ("paper_2609_14668_b300/csrc/update.cuh",
-                          "d3929de7e731b841b1a169c13348f06eff6e9aaf9c794d93243a4fff4cb4c0bd",
-                          10.734848e6 + 0.096256e6),
+                          "c76ababa5c8e37f55e01ef2871eed5f0b40d437a81dd075e09282893bed3c9a3",
+                          10.744832e6 + 0.117760e6),
 }
 
 

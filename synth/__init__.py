@@ -21,9 +21,11 @@ WORKLOADS = {
     # same N and kernels as the headline workload, 16 slices: small device
     # footprint for profiler captures
     "L24_beta1.6": dict(L=24, beta=1.6, dtau=0.1, U=3.73, n_delay=64, n_stab=8),
-    # the headline shape with the charge-channel field (complex G, hs_channel = 1)
-    "L24_beta24_charge": dict(L=24, beta=24.0, dtau=0.1, U=3.73, n_delay=64, n_stab=8, hs_channel=1),
-    "L24_beta1.6_charge": dict(L=24, beta=1.6, dtau=0.1, U=3.73, n_delay=64, n_stab=8, hs_channel=1),
+    # the charge-channel field (complex G held as its 2N x 2N real embedding,
+    # hs_channel = 1) at the largest beta t = L lattice whose embedding fits the
+    # column kernels (2N <= 2048), and the spin channel on the same lattice
+    "L21_beta21_charge": dict(L=21, beta=21.0, dtau=0.1, U=3.73, n_delay=64, n_stab=7, hs_channel=1),
+    "L21_beta21": dict(L=21, beta=21.0, dtau=0.1, U=3.73, n_delay=64, n_stab=7),
 }
 
 
