@@ -379,11 +379,11 @@ def time_chain(pkg, torch, args, key, precision, rank, world, dev, dist, stream)
 # (profiles/k_update_slice_L24.md: same N and n_delay as the L=24 workload).
 CAPTURED_TRAFFIC = {
     ("update", 1, 1152): ("paper_2609_14668_b300/csrc/update.cuh",
-                          "c76ababa5c8e37f55e01ef2871eed5f0b40d437a81dd075e09282893bed3c9a3",
-                          10.744832e6 + 0.117760e6),
+                          "e92dc84aa584f90166e773f371e8ddb8498d8069c294426bdb467acea7b233b9",
+                          10.734080e6 + 0.216832e6),
     ("update", 3, 1152): ("paper_2609_14668_b300/csrc/update.cuh",
-                          "c76ababa5c8e37f55e01ef2871eed5f0b40d437a81dd075e09282893bed3c9a3",
-                          10.744832e6 + 0.117760e6),
+                          "e92dc84aa584f90166e773f371e8ddb8498d8069c294426bdb467acea7b233b9",
+                          10.734080e6 + 0.216832e6),
 }
 
 

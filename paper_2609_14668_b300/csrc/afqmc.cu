@@ -251,6 +251,11 @@ void launch_rowop(afqmc_handle* h, const double* in, double* out, int nrows, Op 
     CK(cudaGetLastError());
 }
 
+// The slice kernel of the handle's field: spin channel (0) or charge channel (1).
+const void* upd_kernel(int charge) {
+    return charge ? (const void*)k_update_slice<1> : (const void*)k_update_slice<0>;
+}
+
 DiagScale no_scale() { return DiagScale{nullptr, 1.0, 1.0}; }
 // The diagonal factor of B_l.  Spin channel: e^{spin_sign gamma s_l} (real).
 // Charge channel: the complex factor e^{charge_sign i alpha s_l} by which the
@@ -478,7 +483,7 @@ void update_slice(afqmc_handle* h, double* G, int l, int pass, int64_t sweep, co
     a.pair = h->cplx; a.Np = h->Np;
     a.force = force; a.logR = logR; a.two_gamma = h->charge ? 0.0 : 2.0 * h->gamma;
     a.dl_p = h->dl_p; a.dl_m = h->dl_m; a.ef_p = h->ef_p; a.ef_m = h->ef_m;
-    a.charge = h->charge; a.dli_p = h->dli_p; a.dli_m = h->dli_m;
+    a.dli_p = h->dli_p; a.dli_m = h->dli_m;
     a.key = h->key;
     a.ctr_stride = 2ull * (uint64_t)h->M * (uint64_t)h->Np;
     a.ctr0 = ((uint64_t)pass * (uint64_t)h->M + (uint64_t)(l - 1)) * (uint64_t)h->Np + 1;
@@ -489,7 +494,7 @@ void update_slice(afqmc_handle* h, double* G, int l, int pass, int64_t sweep, co
     const size_t smem = update_smem(h->W, h->nd, h->p.precision, h->N, h->upd_grid);
     void* args[] = {&a};
     Scope sc(h, AFQMC_K_UPDATE);
-    CK(cudaLaunchCooperativeKernel((void*)k_update_slice, h->upd_grid, UPD_THREADS, args, smem, h->stream));
+    CK(cudaLaunchCooperativeKernel(upd_kernel(h->charge), h->upd_grid, UPD_THREADS, args, smem, h->stream));
 }
 
 void measure(afqmc_handle* h, const double* G, bool accumulate) {
@@ -732,9 +737,9 @@ afqmc_status noalloc_setup(int dev, size_t smem) {
     }
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = raise_smem_limit((const void*)k_update_slice, smem);
+    if (e == cudaSuccess) e = raise_smem_limit(upd_kernel(0), smem);
     int occ = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_slice, UPD_THREADS, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, upd_kernel(0), UPD_THREADS, smem);
     if (e != cudaSuccess || occ < 1) {
         g_create_error = std::string("update kernel set-up failed: ") + cudaGetErrorString(e);
         return AFQMC_E_CUDA;
@@ -845,9 +850,9 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
             CK(raise_smem_limit(f, cpb_smem(N)));
         h->upd_grid = P.update_ctas > 0 ? P.update_ctas : h->sms;
         const size_t usmem = update_smem(h->W, h->nd, P.precision, N, h->upd_grid);
-        CK(raise_smem_limit((const void*)k_update_slice, usmem));
+        CK(raise_smem_limit(upd_kernel(h->charge), usmem));
         int occ = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_slice, UPD_THREADS, usmem));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, upd_kernel(h->charge), UPD_THREADS, usmem));
         if (occ < 1) throw CudaFail{AFQMC_E_INVALID, "update kernel does not fit on an SM"};
         if (h->upd_grid > occ * h->sms) throw CudaFail{AFQMC_E_INVALID, "update_ctas exceeds the co-resident CTAs of the device"};
         {
@@ -1240,7 +1245,7 @@ afqmc_status afqmc_update_slice_noalloc(double* G_dev, int8_t* s_dev, int32_t N,
     e = cudaMemsetAsync(base, 0, NA_OFF_CTL, stream);
     void* args[] = {&a};
     if (e == cudaSuccess)
-        e = cudaLaunchCooperativeKernel((void*)k_update_slice, g_noalloc_sms[dev], UPD_THREADS, args, smem, stream);
+        e = cudaLaunchCooperativeKernel(upd_kernel(0), g_noalloc_sms[dev], UPD_THREADS, args, smem, stream);
     DevStatus ds{};
     unsigned long long acc = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&ds, a.st, sizeof(ds), cudaMemcpyDeviceToHost, stream);

@@ -62,7 +62,6 @@ struct UpdArgs {
     const int8_t* force;
     double* logR;
     double two_gamma;
-    int charge;                   // 1: charge-channel field (complex Delta, pair mode)
     double dli_p, dli_m;          // Im Delta for s = +1, -1 (charge channel)
 };
 
@@ -262,6 +261,9 @@ __device__ bool flush_tile_tcgen05(const UpdArgs& a, int k, int i0, int j0, unsi
     return true;
 }
 
+// CHARGE = 1: charge-channel field (complex Delta, pair mode); a template
+// parameter so that the spin-channel kernel carries none of its code.
+template <int CHARGE>
 __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
     extern __shared__ double upd_smem[];
     const int N = a.N, W = a.W, nd = a.nd;
@@ -322,7 +324,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                     vv[t] = u * (sg > 0 ? a.ef_m : a.ef_p);
                 }
                 dd[t] = sg > 0 ? a.dl_p : a.dl_m;
-                od[t] = a.charge ? (sg > 0 ? a.dli_p : a.dli_m) : 1.0 + dd[t];
+                od[t] = CHARGE ? (sg > 0 ? a.dli_p : a.dli_m) : 1.0 + dd[t];
                 sw[t] = (int8_t)sg;
             }
             __syncthreads();
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                     double c = 0.0, c2 = 0.0;
                     for (; t0 < nw; ++t0) {
                         const double dl = dd[t0];
-                        if (a.charge) {
+                        if constexpr (CHARGE != 0) {
                             // one complex flip per pair (t0 even): G_pp = Gw[t0][t0] + i Gw[t0+1][t0],
                             // r = 1 + Delta (1 - G_pp), R = |r|^2, kappa = Delta conj(r) / |r|^2
                             const double di = od[t0];
@@ -387,7 +389,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                             break;
                         }
                     }
-                    if (found >= 0) t0 += a.charge ? 2 : 1;
+                    if (found >= 0) t0 += CHARGE ? 2 : 1;
                     s_found[slot] = found;
                     s_c[slot] = c;
                     s_c2[slot] = c2;
@@ -396,7 +398,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                 const int tf = s_found[slot];
                 if (tf < 0) break;
                 const double c = s_c[slot];
-                if (a.charge) {
+                if constexpr (CHARGE != 0) {
                     // the pair (tf, tg) as two simultaneous real moves (x1, y1), (x2, y2)
                     const double c2 = s_c2[slot];
                     const int tg = tf + 1;
@@ -574,7 +576,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                 double ax = mine ? g_jm - (ox0 + ox1) : 0.0;
                 double ay = mine ? (j == im ? 1.0 : 0.0) - g_mj + (oy0 + oy1) : 0.0;
                 double xv = 0.0, yv = 0.0;
-                if (a.charge) {
+                if constexpr (CHARGE != 0) {
                     // moves come in pairs (q, q + 1) of one complex flip: both take the
                     // columns and rows as they were before the pair, x mixes them by kappa
                     for (int q = 0; q + 1 < nn; q += 2) {
@@ -589,14 +591,15 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                             ay = fma(sxw[q * W + tm], y0, fma(sxw[(q + 1) * W + tm], y1, ay));
                         }
                     }
-                }
-                for (int q = 0; q < nn && !a.charge; ++q) {
-                    if (lane == q) { xv = cm * ax; yv = ay; }
-                    const double xq = __shfl_sync(0xffffffffu, xv, q);
-                    const double yq = __shfl_sync(0xffffffffu, yv, q);
-                    if (mine && lane > q) {
-                        ax = fma(-xq, syw[q * W + tm], ax);
-                        ay = fma(sxw[q * W + tm], yq, ay);
+                } else {
+                    for (int q = 0; q < nn; ++q) {
+                        if (lane == q) { xv = cm * ax; yv = ay; }
+                        const double xq = __shfl_sync(0xffffffffu, xv, q);
+                        const double yq = __shfl_sync(0xffffffffu, yv, q);
+                        if (mine && lane > q) {
+                            ax = fma(-xq, syw[q * W + tm], ax);
+                            ay = fma(sxw[q * W + tm], yq, ay);
+                        }
                     }
                 }
                 if (mine) {
