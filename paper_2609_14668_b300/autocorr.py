@@ -1,4 +1,5 @@
-"""Integrated autocorrelation time of Monte Carlo time series (host-side analysis).
+"""Integrated autocorrelation time and binning error bars of Monte Carlo time
+series (host-side analysis).
 
 Convention (Sokal, "Monte Carlo methods in statistical mechanics", 1997):
 tau_int = 1/2 + sum_{t>=1} rho(t), so uncorrelated samples have tau_int = 1/2
@@ -48,3 +49,36 @@ def tau_int(series_list, c=6.0):
         if w >= c * tau:
             return max(tau, 0.5), w, n
     return max(tau, 0.5), -1, n
+
+
+def binning_errors(series):
+    """Standard errors of the mean of a correlated series by binning (the
+    'standard binning analysis' of Sec. II.B for Monte Carlo error bars): the
+    series is averaged in blocks of 1, 2, 4, ... consecutive samples and the
+    naive standard error of the block means is returned for every block size
+    with at least 16 blocks.  For correlated samples the error grows with the
+    block size and levels off at the true one, sqrt(2 tau_int) times the naive
+    value.  Returns (block sizes, errors)."""
+    x = np.asarray(series, dtype=np.float64)
+    sizes, errs = [], []
+    b = 1
+    while len(x) // b >= 16:
+        nb = len(x) // b
+        means = x[: nb * b].reshape(nb, b).mean(axis=1)
+        sizes.append(b)
+        errs.append(float(means.std(ddof=1) / np.sqrt(nb)))
+        b *= 2
+    return np.array(sizes, dtype=int), np.array(errs)
+
+
+def binned_error(series, min_blocks=32):
+    """Error bar of the mean: the binning error at the largest block size that
+    still leaves at least min_blocks blocks (0 for fewer than 2 samples)."""
+    x = np.asarray(series, dtype=np.float64)
+    if len(x) < 2:
+        return 0.0
+    sizes, errs = binning_errors(x)
+    if len(sizes) == 0:
+        return float(x.std(ddof=1) / np.sqrt(len(x)))
+    ok = [e for s, e in zip(sizes, errs) if len(x) // s >= min_blocks]
+    return float(ok[-1] if ok else errs[0])

@@ -40,3 +40,36 @@ def test_degenerate_series():
     # a monotone series stays positively correlated at short lags
     tau, w, n = tau_int([np.arange(40.0)])
     assert tau > 2.0 and n == 40
+
+
+def test_binning_of_independent_samples_is_flat():
+    """i.i.d. samples: every block size gives the naive error sigma / sqrt(n)."""
+    from paper_2609_14668_b300.autocorr import binning_errors, binned_error
+    x = np.random.default_rng(3).standard_normal(1 << 16)
+    sizes, errs = binning_errors(x)
+    assert sizes[0] == 1 and sizes[-1] == (1 << 16) // 16
+    naive = x.std(ddof=1) / np.sqrt(len(x))
+    assert errs[0] == pytest.approx(naive)
+    assert np.all(np.abs(errs[:8] / naive - 1.0) < 0.15)
+    assert abs(binned_error(x) / naive - 1.0) < 0.3
+
+
+@pytest.mark.parametrize("rho", [0.5, 0.8])
+def test_binning_of_ar1_reaches_the_correlated_error(rho):
+    """AR(1): the error of the mean is sigma_x sqrt(2 tau_int / n) with
+    sigma_x^2 = 1 / (1 - rho^2) and 2 tau_int = (1 + rho) / (1 - rho)."""
+    from paper_2609_14668_b300.autocorr import binned_error
+    n = 1 << 17
+    x = ar1(rho, n, 5)
+    exact = np.sqrt(1.0 / (1.0 - rho * rho) * (1.0 + rho) / (1.0 - rho) / n)
+    assert abs(binned_error(x) / exact - 1.0) < 0.2
+    naive = x.std(ddof=1) / np.sqrt(n)
+    assert binned_error(x) > 1.5 * naive
+
+
+def test_binning_degenerate():
+    from paper_2609_14668_b300.autocorr import binned_error, binning_errors
+    assert binned_error([1.0]) == 0.0
+    s, e = binning_errors(np.arange(10.0))
+    assert len(s) == 0
+    assert binned_error(np.arange(10.0)) == pytest.approx(np.arange(10.0).std(ddof=1) / np.sqrt(10))
