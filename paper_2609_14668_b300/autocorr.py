@@ -82,3 +82,21 @@ def binned_error(series, min_blocks=32):
         return float(x.std(ddof=1) / np.sqrt(len(x)))
     ok = [e for s, e in zip(sizes, errs) if len(x) // s >= min_blocks]
     return float(ok[-1] if ok else errs[0])
+
+
+def twist_average(means, errors=None):
+    """Twist-averaged estimate (Sec. III.C): the plain mean over the N_Theta twisted
+    chains.  The chains are independent and each has its own expectation, so the
+    statistical error of the average comes from the chains' own error bars,
+    sqrt(sum_i err_i^2) / N_Theta, not from the spread between twists (which is
+    the boundary-condition dependence TABC averages out).  Returns (mean, error);
+    error is None without per-chain errors."""
+    m = np.asarray(means, dtype=np.float64)
+    if m.size == 0:
+        raise ValueError("no twists")
+    avg = float(m.mean(axis=0)) if m.ndim == 1 else m.mean(axis=0)
+    if errors is None:
+        return avg, None
+    e = np.asarray(errors, dtype=np.float64)
+    err = np.sqrt((e * e).sum(axis=0)) / m.shape[0]
+    return avg, (float(err) if np.ndim(err) == 0 else err)

@@ -73,3 +73,21 @@ def test_binning_degenerate():
     s, e = binning_errors(np.arange(10.0))
     assert len(s) == 0
     assert binned_error(np.arange(10.0)) == pytest.approx(np.arange(10.0).std(ddof=1) / np.sqrt(10))
+
+
+def test_twist_average_error_from_chain_errors():
+    """Independent chains with different expectations: the error of the twist
+    average is sqrt(sum err_i^2) / N, checked by repeating the experiment."""
+    from paper_2609_14668_b300.autocorr import twist_average
+    rng = np.random.default_rng(9)
+    mu = np.linspace(-1.0, 1.0, 14)              # per-twist expectations
+    sig = np.linspace(0.05, 0.2, 14)             # per-twist error bars
+    draws = [twist_average(mu + sig * rng.standard_normal(14), sig) for _ in range(4000)]
+    avgs = np.array([d[0] for d in draws])
+    err = draws[0][1]
+    assert err == pytest.approx(np.sqrt((sig ** 2).sum()) / 14)
+    assert abs(avgs.mean() - mu.mean()) < 4 * err / np.sqrt(4000) + 1e-12
+    assert abs(avgs.std() / err - 1.0) < 0.05
+    assert twist_average([1.0, 3.0]) == (2.0, None)
+    with pytest.raises(ValueError):
+        twist_average([])
