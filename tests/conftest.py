@@ -22,3 +22,4 @@ _build_library()
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (B300) and the built libafqmc.so")
     config.addinivalue_line("markers", "slow: CPU test that takes tens of seconds")
+    config.addinivalue_line("markers", "paper: long GPU physics run against the paper's tables (opt-in: -m paper)")
