@@ -378,7 +378,7 @@ def time_chain(pkg, torch, args, key, precision, rank, world, dev, dist, stream)
 
 # DRAM bytes per launch of a kernel family from one ncu capture, valid only while
 # the kernel's source file still has the hash it had when the counters were taken
-# (profiles/k_update_slice_L24.md: same N and n_delay as the L=24 workload).
+# (an ncu capture of the slice kernel at the L=24 workload's N and n_delay).
 CAPTURED_TRAFFIC = {
     ("update", 1, 1152): ("paper_2609_14668_b300/csrc/update.cuh",
                           "e92dc84aa584f90166e773f371e8ddb8498d8069c294426bdb467acea7b233b9",

@@ -227,7 +227,12 @@ afqmc_status afqmc_get_timing(afqmc_handle* h, afqmc_timing* out);
  * host allocator or a memory-pool callback, in a process whose device memory
  * is entirely owned by another framework's caching allocator, or under a
  * strict no-allocation policy for a real-time loop).  The paper has no
- * counterpart; it computes exactly what afqmc_update_slice computes.
+ * counterpart.  It covers one form only: the periodic, spin-channel chain
+ * (real G, N = 2 L^2 physical sites) with the FP64 flush.  For that form it
+ * computes what afqmc_update_slice computes on a handle created with
+ * theta = (0, 0), hs_channel = 0 and precision 0 or 2; twisted,
+ * charge-channel and split-TF32 (precision bit 0) handles compute something
+ * else and have no allocation-free variant.
  *
  * The caller passes device pointers on the current device: G_dev (N*N FP64,
  * row-major, read and overwritten with the updated G) and s_dev (the N int8
@@ -243,11 +248,13 @@ afqmc_status afqmc_get_timing(afqmc_handle* h, afqmc_timing* out);
  *
  * The first call on a device does a one-time set-up on that device (looks up
  * the device address of the scratch array and sets the kernel's shared-memory
- * limit); make that first call before any stream capture.  Every call shares
- * the one scratch array, so calls that overlap on the GPU (different streams
- * or threads at the same time) race; serialise them.  The call enqueues on
- * cuda_stream (NULL = legacy default stream) and synchronises it before
- * returning; *n_accepted (may be NULL) receives the number of accepted flips. */
+ * limit); that first call should come before any stream capture begins.
+ * Every call shares the one scratch array, so calls that overlap on the GPU
+ * (different streams or threads at the same time) race; serialise them.  The
+ * call enqueues on cuda_stream (NULL = legacy default stream), copies the
+ * status and the accepted count to host memory and synchronises the stream
+ * before returning; *n_accepted (may be NULL) receives the number of accepted
+ * flips. */
 afqmc_status afqmc_update_slice_noalloc(double* G_dev, int8_t* s_dev, int32_t N, int32_t M, int32_t slice,
                                         int32_t pass, uint64_t sweep_index, double U, double dtau,
                                         int32_t n_delay, uint64_t seed, int32_t chain, void* cuda_stream,

@@ -6,7 +6,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libafqmc.so")
 SOURCES = ["csrc/afqmc.cu"]
-HEADERS = ["csrc/common.cuh", "csrc/linalg.cuh", "csrc/measure.cuh", "csrc/update.cuh", "csrc/wrap.cuh"]
+HEADERS = ["csrc/common.cuh", "csrc/learned.cuh", "csrc/linalg.cuh", "csrc/measure.cuh", "csrc/ozaki.cuh",
+           "csrc/tdgf.cuh", "csrc/update.cuh", "csrc/wrap.cuh"]
 
 
 def nvcc_command(out=LIB):
@@ -34,20 +35,5 @@ def build(force=False, verbose=False):
     return LIB
 
 
-def build_peak(verbose=False):
-    """Standalone FP64/FP32/barrier microbenchmark (fp64_peak)."""
-    out = os.path.join(HERE, "fp64_peak")
-    nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
-    cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", out, os.path.join(HERE, "csrc", "fp64_peak.cu")]
-    if verbose:
-        print(" ".join(cmd))
-    subprocess.run(cmd, check=True)
-    return out
-
-
 if __name__ == "__main__":
-    import sys
-    if "--peak" in sys.argv:
-        build_peak(verbose=True)
-    else:
-        build(force=True, verbose=True)
+    build(force=True, verbose=True)
