@@ -168,7 +168,10 @@ afqmc_status afqmc_sweep(afqmc_handle* h, int32_t n_sweeps, afqmc_sweep_stats* s
 afqmc_status afqmc_measure(afqmc_handle* h, afqmc_obs* out, double* Czz, double* nk);
 
 /* Averages of the measurements accumulated during sweeps since the last call
- * (params.measure = 1), then reset.  n_samples = 0 if none.  Arrays as above. */
+ * (params.measure = 1), then reset.  n_samples = 0 if none.  Arrays as above.
+ * R_m2 here is the correlation ratio of the averages,
+ * 1 - <S_zz(Gamma + b1/L1)> / <S_zz(Gamma)> (Eq. CrfRatio is defined on
+ * expectation values), not the mean of per-field ratios. */
 afqmc_status afqmc_get_obs(afqmc_handle* h, afqmc_obs* out, double* Czz, double* nk);
 
 /* G at slice l (0 <= l <= M) recomputed from scratch for the current field by

@@ -63,6 +63,27 @@ def _observables_diag(occ_u, occ_d, U, bravais_pairs):
     return docc, hu, czz
 
 
+def _structure_diag(occ_u, occ_d, lat):
+    """Spin structure factor of every basis state, computed directly from the
+    spin density (no detour through C_zz): for each k = (l1/L1) b1 + (l2/L2) b2,
+    S(k) = (|sum_{i in A} e^{ik.r_i} s_i|^2 + |sum_{i in B} e^{ik.r_i} s_i|^2) / (2 N_c),
+    r_i the Bravais vector of site i's cell, s_i = (n_up - n_dn)/2.  Summed over
+    i and j of one sublattice this is the double sum that Eq. SpinStrucF applied
+    to Eq. SzSzCrF amounts to on the periodic lattice.  Shape (du, dd, N_c),
+    k index l1 + L1 * l2."""
+    Nc, L1, L2 = lat.Nc, lat.L1, lat.L2
+    sz = 0.5 * (occ_u[:, None, :] - occ_d[None, :, :])
+    ph = np.empty((Nc, Nc), dtype=complex)           # ph[k, cell] = e^{i k.r_cell}
+    for l2 in range(L2):
+        for l1 in range(L1):
+            for c in range(Nc):
+                n1, n2 = lat.cell_coords(c)
+                ph[l1 + L1 * l2, c] = np.exp(2j * np.pi * (l1 * n1 / L1 + l2 * n2 / L2))
+    amp_a = sz[..., :Nc] @ ph.T
+    amp_b = sz[..., Nc:] @ ph.T
+    return (np.abs(amp_a) ** 2 + np.abs(amp_b) ** 2) / (2.0 * Nc)
+
+
 def bravais_pair_table(lat):
     """For C_zz(r): r=(d1,d2) -> list of site pairs (i, i+r) on the same sublattice."""
     out = {}
@@ -84,6 +105,8 @@ def trotter_averages(lat, K, U, dtau, M):
     Z = 0.0
     acc_d = acc_kin = acc_n1 = acc_n2 = 0.0
     acc_c = {k: 0.0 for k in pairs}
+    acc_s = np.zeros(lat.Nc)
+    acc_m = 0.0
     for nu in range(N + 1):
         for nd in range(N + 1):
             Ku, Kd, ou, od = _sector_data(K, N, nu, nd)
@@ -107,6 +130,11 @@ def trotter_averages(lat, K, U, dtau, M):
             acc_d += (docc * diag).sum()
             for key in pairs:
                 acc_c[key] += (czz[key] * diag).sum()
+            acc_s += np.real((_structure_diag(ou, od, lat) * diag[..., None]).sum(axis=(0, 1)))
+            # squared sublattice magnetisations (sum_{i in A} s_i)^2 + (sum_{i in B} s_i)^2
+            sz = 0.5 * (ou[:, None, :] - od[None, :, :])
+            ms = sz[..., :lat.Nc].sum(axis=2) ** 2 + sz[..., lat.Nc:].sum(axis=2) ** 2
+            acc_m += np.real((ms * diag).sum())
             KX = np.tensordot(Ku, X, axes=(1, 0)) + np.matmul(Kd, X)
             acc_kin += KX[ia, ib, np.arange(du * dd)].sum()
     # with a twist the sector matrices are complex; the traces are real up to rounding
@@ -119,7 +147,11 @@ def trotter_averages(lat, K, U, dtau, M):
         Czz[d2, d1] = np.real(v) / Z / (2.0 * lat.Nc)
     # Eq. ChiCharge: (beta / N_s) (<N^2> - <N>^2), beta = M dtau
     chi_e = M * dtau / N * (acc_n2 / Z - (acc_n1 / Z) ** 2)
-    return dict(double_occ=D, energy=(ekin + N * U * D) / N, ekin=ekin / N, Czz=Czz, chi_e=chi_e)
+    # S_zz(k) from the spin density itself, and m^2 = <M_A^2 + M_B^2> / (2 N_c)^2
+    # (the Neel order parameter squared, Sec. II.C below Eq. SpinStrucF)
+    Szz = (acc_s / Z).reshape(lat.L2, lat.L1)
+    m2 = acc_m / Z / (2.0 * lat.Nc) ** 2
+    return dict(double_occ=D, energy=(ekin + N * U * D) / N, ekin=ekin / N, Czz=Czz, chi_e=chi_e, Szz=Szz, m2=m2)
 
 
 def thermal_averages(lat, K, U, beta):

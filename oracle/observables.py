@@ -11,7 +11,13 @@ the asymmetric Trotter product.  Readings:
     n_ia = 1 - G^a_ii,  <c_i^+ c_j> = delta_ij - G_ji;
   * with a twist G is complex for one field: every Wick product is formed in
     complex arithmetic and its real part taken at the end (the weight is real
-    and positive, and the imaginary parts average to zero).
+    and positive, and the imaginary parts average to zero);
+  * R_m2 returned for one G is the per-field ratio 1 - S(Gamma+dk)/S(Gamma),
+    used only for fixed-field parity; over many configurations Eq. CrfRatio
+    is taken on the averages, 1 - <S(Gamma+dk)> / <S(Gamma)>.
+Pins: tests/test_oracle_pins.py (exhaustive HS sum against Fock-space ED for
+C_zz, S_zz(Gamma), S_zz(Gamma + b1/L), m^2, C_zz(L/2, 0); free-fermion closed
+forms for S_zz, m^2, n(k), D, e, chi_e).
 """
 import numpy as np
 

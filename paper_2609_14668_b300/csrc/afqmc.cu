@@ -1053,6 +1053,8 @@ afqmc_status afqmc_get_obs(afqmc_handle* h, afqmc_obs* out, double* Czz, double*
     if (s != AFQMC_OK) return s;
     const double inv = n > 0 ? 1.0 / (double)n : 0.0;
     for (double& x : v) x *= inv;
+    // Eq. CrfRatio on expectation values: the ratio of the averaged structure factors
+    v[7] = (n > 0 && v[5] != 0.0) ? 1.0 - v[6] / v[5] : 0.0;
     fill_obs(v, n, out);
     if (Czz) for (int d = 0; d < h->Nc; ++d) Czz[d] = cz[d] * inv;
     if (nk) for (size_t q = 0; q < nkv.size(); ++q) nk[q] = nkv[q] * inv;

@@ -152,6 +152,8 @@ def test_sweep_measurements_accumulate(pkg):
     assert o["n_samples"] == 2 * 2 * (30 // 10)
     assert abs(o["density"] - 1.0) < 1e-12
     assert 0.0 < o["double_occ"] < 0.25
+    # correlation ratio of the averaged structure factors (Eq. CrfRatio on expectation values)
+    assert abs(o["R_m2"] - (1.0 - o["S_af_dk"] / o["S_af"])) < 1e-14
     o2 = ch.observables()
     assert o2["n_samples"] == 0
     ch.close()

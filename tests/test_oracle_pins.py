@@ -234,15 +234,41 @@ def test_uniforms_in_unit_interval():
 
 
 # ---------------------------------------------------------------- exact diagonalisation
+SF_KEYS = ("S_af", "S_af_dk", "m2", "Czz_half")
+
+
+def check_structure_factor(m, got, ref, twisted):
+    """The oracle's structure-factor step (Eqs. SzSzCrF, SpinStrucF, CrfRatio and
+    m^2 = S_zz(Gamma)/(2 N_c)) against the Fock-space structure factor computed
+    from the spin density directly (oracle.ed, |sum_i e^{ik.r_i} s_i|^2 per
+    sublattice; no C_zz involved): S_zz(Gamma), S_zz(Gamma + b1/L), m^2 and
+    C_zz(floor(L/2), 0), all as exact averages over every HS field.  R_m^2 of a
+    set of configurations is 1 - <S_zz(Gamma + dk)> / <S_zz(Gamma)> (the ratio of
+    the expectation values, as Eq. CrfRatio defines it)."""
+    S = ref["Szz"]                                    # [l2, l1]
+    assert abs(got["S_af"] - S[0, 0]) < 1e-10
+    assert abs(got["S_af_dk"] - S[0, 1]) < 1e-10      # dk = b1 / L: l1 = 1, l2 = 0
+    assert abs(got["m2"] - ref["m2"]) < 1e-12
+    assert abs(got["Czz_half"] - ref["Czz"][0, m.lat.L1 // 2]) < 1e-10
+    R_ed = 1.0 - S[0, 1] / S[0, 0]
+    assert abs((1.0 - got["S_af_dk"] / got["S_af"]) - R_ed) < 1e-9
+    if twisted:
+        # the twist breaks the a1 <-> a2 symmetry: dk along b2 or C_zz along a2
+        # would fail the checks above by far more than their tolerance
+        assert abs(S[0, 1] - S[1, 0]) > 1e-6
+        assert abs(ref["Czz"][0, 1] - ref["Czz"][1, 0]) > 1e-6
+
+
 @pytest.mark.slow
 def test_hs_sum_equals_trotter_ed():
     """Exhaustive HS sum (oracle weights + Wick) equals the Trotterised Fock-space ED exactly (L=2, 8 sites, M=2)."""
     m = Model(2, U=4.0, beta=0.4, dtau=0.2)
     ref = ed.trotter_averages(m.lat, m.K, m.U, m.dtau, m.M)
-    got = hs_enum.hs_average(m, keys=("double_occ", "energy", "ekin", "Czz", "chi_e"))
+    got = hs_enum.hs_average(m, keys=("double_occ", "energy", "ekin", "Czz", "chi_e") + SF_KEYS)
     for k in ("double_occ", "energy", "ekin", "chi_e"):
         assert abs(got[k] - ref[k]) < 1e-10
     assert np.abs(got["Czz"] - ref["Czz"]).max() < 1e-10
+    check_structure_factor(m, got, ref, twisted=False)
 
 
 def test_trotter_ed_converges_to_thermal_ed():
@@ -374,10 +400,30 @@ def test_hs_sum_equals_trotter_ed_twisted():
     e^{-gamma sum s}|det|^2 and complex Wick contractions equals the Trotterised ED."""
     m = Model(2, U=4.0, beta=0.4, dtau=0.2, theta=TW)
     ref = ed.trotter_averages(m.lat, m.K, m.U, m.dtau, m.M)
-    got = hs_enum.hs_average(m, keys=("double_occ", "energy", "ekin", "Czz", "chi_e"))
+    got = hs_enum.hs_average(m, keys=("double_occ", "energy", "ekin", "Czz", "chi_e") + SF_KEYS)
     for k in ("double_occ", "energy", "ekin", "chi_e"):
         assert abs(got[k] - ref[k]) < 1e-10
     assert np.abs(got["Czz"] - ref["Czz"]).max() < 1e-10
+    check_structure_factor(m, got, ref, twisted=True)
+
+
+@pytest.mark.parametrize("L", [3, 6])
+@pytest.mark.parametrize("theta", [(0.0, 0.0), TW])
+def test_U0_structure_factor_closed_form(L, theta):
+    """Free fermions at half filling: the spins are independent and the diagonal
+    of the per-spin Fermi matrix (1 + e^{beta h(k)})^-1 is 1/2 at every k (h(k)
+    has a zero diagonal), so <c_i^+ c_j> = delta_ij / 2 within a sublattice and
+    <s_i s_j> = delta_ij / 8 there.  Hence S_zz(k) = 1/8 at every k,
+    m^2 = 1 / (16 N_c), C_zz(r != 0) = 0 and R_m^2 = 0."""
+    m = Model(L, U=0.0, beta=float(L), dtau=0.1, theta=theta)
+    o = measure(m, m.green_stable(random_field(m.M, m.N, 4), 0, 10))
+    assert abs(o["S_af"] - 0.125) < 1e-12 and abs(o["S_af_dk"] - 0.125) < 1e-12
+    assert abs(o["m2"] - 1.0 / (16 * m.lat.Nc)) < 1e-14
+    assert abs(o["R_m2"]) < 1e-11
+    assert abs(o["Czz"][0, 0] - 0.125 / 1.0) < 1e-12
+    off = o["Czz"].copy()
+    off[0, 0] = 0.0
+    assert np.abs(off).max() < 1e-12
 
 
 @pytest.mark.parametrize("theta", [(0.0, 0.0), TW])
