@@ -221,6 +221,16 @@ afqmc_status afqmc_set_timing(afqmc_handle* h, int32_t family_mask);
  * cover every family, the times only the timed ones (0 for the others). */
 afqmc_status afqmc_get_timing(afqmc_handle* h, afqmc_timing* out);
 
+/* Test hook for the failure paths (no counterpart in the paper): the limit, in
+ * nanoseconds, of every device-side wait between CTAs of this handle's kernels
+ * (grid barriers of the cooperative kernels, the column hand-offs of the QR and
+ * LU).  0 restores the default of 2 s.  A wait that runs out sets the handle's
+ * device error flag and its kernel returns; the next call that checks the
+ * device returns AFQMC_E_TIMEOUT and every later call AFQMC_E_STATE.  Waits on
+ * the tensor cores' own completion keep the 2 s limit.  Synchronises the
+ * stream. */
+afqmc_status afqmc_set_wait_limit(afqmc_handle* h, uint64_t wait_ns);
+
 /* Largest sizes accepted by afqmc_update_slice_noalloc. */
 #define AFQMC_NOALLOC_MAX_N 1152
 #define AFQMC_NOALLOC_MAX_NDELAY 64

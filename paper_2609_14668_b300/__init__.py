@@ -79,6 +79,7 @@ _SIGS = {
     "afqmc_det_ratio": ([_H, ctypes.c_int32, ctypes.c_int32, _DP]),
     "afqmc_dims": ([_H, _P(ctypes.c_int32), _P(ctypes.c_int32), _P(ctypes.c_int32)]),
     "afqmc_set_timing": ([_H, ctypes.c_int32]),
+    "afqmc_set_wait_limit": ([_H, ctypes.c_uint64]),
     "afqmc_update_slice_noalloc": ([_DP, _I8P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.c_uint64, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
                                     ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p, _P(ctypes.c_int32)]),
@@ -245,6 +246,11 @@ def afqmc_det_ratio(h, slice_, site):
 
 
 TIMING_ALL = (1 << len(KERNEL_FAMILIES)) - 1
+
+
+def afqmc_set_wait_limit(h, wait_ns):
+    """Test hook: limit (ns) of the device-side waits between CTAs; 0 = default."""
+    _check(_lib.afqmc_set_wait_limit(h, int(wait_ns)), h)
 
 
 def afqmc_set_timing(h, families):

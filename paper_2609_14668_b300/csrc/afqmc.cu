@@ -6,6 +6,7 @@
 // Carlo path runs in the kernels of wrap.cuh, update.cuh, linalg.cuh and
 // measure.cuh.
 #include <cmath>
+#include <cstddef>
 #include <complex>
 #include <cstdio>
 #include <cstring>
@@ -1081,13 +1082,17 @@ afqmc_status afqmc_wrap_matrix(afqmc_handle* h, int32_t slice, int32_t direction
     if (!A || slice < 1 || slice > h->M || direction < -1 || direction > 1) { h->err = "bad arguments"; return AFQMC_E_INVALID; }
     double* d = h->Wk[3];
     from_host(h, A, d, h->Wk[2]);
+    double* res = d;
     if (direction == 0) {
         half_step(h, d, h->Wk[5]);
-        to_host(h, h->Wk[5], A, h->Wk[2]);
+        res = h->Wk[5];
     } else {
         wrap(h, d, slice, direction);
-        to_host(h, d, A, h->Wk[2]);
     }
+    // a non-finite input propagates through the transforms: report it
+    { Scope sc(h, AFQMC_K_MISC); k_check_finite<<<h->sms * 2, 256, 0, h->stream>>>(res, (size_t)h->N * h->N, h->st, 106); }
+    CK(cudaGetLastError());
+    to_host(h, res, A, h->Wk[2]);
     return check_device(h);
     API_END(h)
 }
@@ -1166,6 +1171,16 @@ afqmc_status afqmc_get_td(afqmc_handle* h, double* C, double* dDdU, double* chiF
     }
     h->td_count = 0;
     return check_device(h);
+    API_END(h)
+}
+
+afqmc_status afqmc_set_wait_limit(afqmc_handle* h, uint64_t wait_ns) {
+    API_BEGIN(h)
+    unsigned long long w = wait_ns;
+    CK(cudaMemcpyAsync(reinterpret_cast<char*>(h->st) + offsetof(DevStatus, wait_ns), &w, sizeof(w),
+                       cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return AFQMC_OK;
     API_END(h)
 }
 

@@ -9,14 +9,26 @@ namespace afq {
 // Error codes written into DevStatus::err by device code (mirrors afqmc_status).
 enum : int { DERR_OK = 0, DERR_NUMERIC = 4, DERR_TIMEOUT = 5 };
 
-// Wall-clock limit of any single device-side wait (nanoseconds).
+// Default wall-clock limit of any single device-side wait (nanoseconds).
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
 
 struct DevStatus {
     int err;            // first error seen (0 = none)
     int where;          // code of the wait that timed out
     unsigned int bar_count, bar_gen;   // grid barrier state
+    // limit of the waits between CTAs (grid barriers, column hand-offs of the
+    // QR and LU); 0 = WAIT_LIMIT_NS.  A test hook can shorten it to make a
+    // wait run out on purpose.  Waits on the tensor cores' own completion
+    // (mbarriers with asynchronous copies or MMAs in flight) keep the fixed
+    // limit: their kernel must not release shared or tensor memory while such
+    // work may still be running.
+    unsigned long long wait_ns;
 };
+
+__device__ __forceinline__ unsigned long long wait_limit(const DevStatus* st) {
+    const unsigned long long w = *(const volatile unsigned long long*)&st->wait_ns;
+    return w ? w : WAIT_LIMIT_NS;
+}
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -36,7 +48,7 @@ __host__ __device__ __forceinline__ double sm64_uniform(uint64_t key, uint64_t n
 }
 
 // Grid-wide barrier for cooperative launches.  Every CTA must call it.  The
-// wait is bounded by WAIT_LIMIT_NS; on timeout the error flag is set and the
+// wait is bounded by wait_limit(st); on timeout the error flag is set and the
 // function returns false, as it does when any CTA has flagged an error.
 __device__ __forceinline__ bool grid_barrier(DevStatus* st, int where) {
     __shared__ int s_ok;
@@ -51,10 +63,10 @@ __device__ __forceinline__ bool grid_barrier(DevStatus* st, int where) {
             __threadfence();
             atomicAdd(&st->bar_gen, 1u);
         } else {
-            unsigned long long t0 = global_ns();
+            const unsigned long long t0 = global_ns(), lim = wait_limit(st);
             while (*vgen == gen) {
                 if (*(volatile int*)&st->err) break;
-                if (global_ns() - t0 > WAIT_LIMIT_NS) {
+                if (global_ns() - t0 > lim) {
                     if (atomicCAS(&st->err, 0, DERR_TIMEOUT) == 0) st->where = where;
                     break;
                 }

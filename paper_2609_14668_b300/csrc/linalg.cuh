@@ -204,10 +204,10 @@ __global__ void __launch_bounds__(256) k_qr_cols(QRArgs q, int cols_in_smem) {
     for (int j = 0; j < n - 1; ++j) {
         if (threadIdx.x == 0) {
             volatile unsigned int* f = q.flags + j;
-            unsigned long long t0 = global_ns();
+            const unsigned long long t0 = global_ns(), lim = wait_limit(q.st);
             while (*f != q.epoch) {
                 if (*(volatile int*)&q.st->err) { s_abort = 1; break; }
-                if (global_ns() - t0 > WAIT_LIMIT_NS) { flag_error(q.st, DERR_TIMEOUT, 101); s_abort = 1; break; }
+                if (global_ns() - t0 > lim) { flag_error(q.st, DERR_TIMEOUT, 101); s_abort = 1; break; }
                 __nanosleep(20);
             }
             __threadfence();
@@ -376,10 +376,10 @@ __global__ void __launch_bounds__(256) k_lu_cols(LUArgs q, int cols_in_smem) {
     for (int j = 0; j < n - 1; ++j) {
         if (threadIdx.x == 0) {
             volatile unsigned int* f = q.flags + j;
-            unsigned long long t0 = global_ns();
+            const unsigned long long t0 = global_ns(), lim = wait_limit(q.st);
             while (*f != q.epoch) {
                 if (*(volatile int*)&q.st->err) { s_abort = 1; break; }
-                if (global_ns() - t0 > WAIT_LIMIT_NS) { flag_error(q.st, DERR_TIMEOUT, 111); s_abort = 1; break; }
+                if (global_ns() - t0 > lim) { flag_error(q.st, DERR_TIMEOUT, 111); s_abort = 1; break; }
             }
             __threadfence();
             s_piv = *(volatile int*)(q.piv + j);
@@ -645,6 +645,14 @@ __global__ void k_set_identity(double* A, int n) {
 __global__ void k_fill(double* a, double v, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] = v;
+}
+
+// Flags DERR_NUMERIC if any of the len values is NaN or infinite.
+__global__ void k_check_finite(const double* __restrict__ A, size_t len, DevStatus* st, int where) {
+    bool bad = false;
+    for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < len; o += (size_t)gridDim.x * blockDim.x)
+        if (!isfinite(A[o])) bad = true;
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) flag_error(st, DERR_NUMERIC, where);
 }
 
 // max |A - B| (elementwise) and NaN detection -> out[0] (atomic max on the bit pattern of a non-negative double).

@@ -1,6 +1,7 @@
 """Batched chains (one CUDA graph per batched sweep), the slice kernel's grid
 knob and the autotuner: all of them change only how the work is scheduled, so
-every chain must end exactly where the same chain swept alone ends."""
+every chain must end exactly where the same chain swept alone ends, and where
+the CPU oracle's chain with the same seed ends."""
 import numpy as np
 import pytest
 
@@ -51,6 +52,31 @@ def test_batch_equals_individual_chains(pkg):
         assert np.array_equal(cb.field(), cs.field())
     for c in singles:
         c.close()
+    batch.close()
+
+
+def test_batch_chains_follow_the_oracle_in_lockstep(pkg):
+    """Every chain of the mixed batch (periodic and twisted, L = 2..6, uneven
+    n_delay and slice-kernel grids) against the CPU oracle's chain with the same
+    seed: after each of two batched sweeps the fields are equal and G at slice 0
+    agrees to 1e-10 (relative), with the same number of accepted flips."""
+    from oracle.dqmc import Model, Chain
+    ps = mixed_params(pkg)
+    batch = pkg.Batch(ps)
+    oracles = [Chain(Model(p.L1, U=p.U, beta=p.beta, dtau=p.dtau, theta=(p.theta1, p.theta2)),
+                     n_delay=p.n_delay, n_stab=p.n_stab, seed=p.seed, chain=p.chain) for p in ps]
+    for cb, oc in zip(batch.chains, oracles):
+        assert np.array_equal(cb.field(), oc.field)
+    for _ in range(2):
+        acc0 = [oc.accepted for oc in oracles]
+        st = batch.sweep(1)
+        for oc in oracles:
+            oc.sweep()
+        assert st.accepted == sum(oc.accepted - a for oc, a in zip(oracles, acc0)) > 0
+        for cb, oc in zip(batch.chains, oracles):
+            assert np.array_equal(cb.field(), oc.field)
+            g = cb.green(0)
+            assert np.abs(g - oc.G).max() <= 1e-10 * np.abs(oc.G).max()
     batch.close()
 
 
