@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default=WORKLOAD_KEY, choices=sorted(WORKLOADS) + ["batched", "learned"],
+    ap.add_argument("--workload", default=WORKLOAD_KEY, choices=sorted(WORKLOADS) + ["batched", "learned", "precision"],
                     help="batched: 64 chains, L in {6, 9, 12}, 16 twists each, one graph per batched sweep")
     ap.add_argument("--no-autotune", action="store_true", help="batched: skip the autotuner (n_delay 16, all SMs)")
     ap.add_argument("--twists", choices=["grid", "quasirandom"], default="grid",
@@ -718,6 +718,91 @@ def run_learned(args):
     print(json.dumps(out))
 
 
+def precision_comparison(pkg, cfg, seed0, sizes=("energy", "double_occ", "S_af", "m2")):
+    """Equilibrium averages of the split-TF32 flush (precision 3) and plain FP64
+    (precision 0) from independent chains, all swept together in one batch:
+    per observable, each precision's mean of chain means and its standard error
+    (chains are independent, so the spread of the chain means carries the
+    autocorrelation), the difference and its z-score."""
+    import numpy as np
+    C = cfg["chains"]
+    plist = []
+    for prec in (3, 0):
+        for c in range(C):
+            plist.append(pkg.make_params(L=cfg["L"], beta=cfg["beta"], dtau=cfg["dtau"], U=cfg["U"],
+                                         n_delay=cfg["n_delay"], n_stab=cfg["n_stab"], seed=seed0 + prec,
+                                         chain=c, measure=1, precision=prec))
+    batch = pkg.Batch(plist)
+    batch.sweep(cfg["warm"])
+    for c in batch.chains:
+        c.observables()
+    series = np.zeros((2 * C, cfg["meas"], len(sizes)))
+    drift = 0.0
+    for s in range(cfg["meas"]):
+        st = batch.sweep(1)
+        drift = max(drift, st.max_stab_drift)
+        for i, c in enumerate(batch.chains):
+            o = c.observables()
+            series[i, s] = [o[k] for k in sizes]
+    batch.close()
+    out = {}
+    for j, k in enumerate(sizes):
+        cm = series[:, :, j].mean(axis=1)
+        a, b = cm[:C], cm[C:]
+        ma, mb = a.mean(), b.mean()
+        sa, sb = a.std(ddof=1) / np.sqrt(C), b.std(ddof=1) / np.sqrt(C)
+        d, sd = ma - mb, float(np.hypot(sa, sb))
+        out[k] = {"tf32": [ma, sa], "fp64": [mb, sb], "diff": d, "sigma": sd, "z": d / sd if sd > 0 else 0.0,
+                  "rel_diff": d / abs(mb) if mb else None}
+    return out, drift
+
+
+def run_precision(args):
+    """The split-TF32 flush against the FP64 flush.  (1) Drift of the wrapped G
+    from its QR recomputation after n_stab slices, n_stab in 1, 2, 4, 8, for
+    both precisions at L = 12 and L = 24 (one chain each, after a warm-up
+    sweep).  (2) Equilibrium e, D, S_AF, m^2 of independent chains of both
+    precisions at L = 12 (and at L = 24 unless --steps 0), as (TF32 - FP64) +- sigma."""
+    import torch
+    import paper_2609_14668_b300 as pkg
+    from synth import PRECISION_STUDY as P
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    drift = {}
+    for key in ("L12", "L24"):
+        cfg = P[key]
+        drift[key] = {}
+        for prec in (3, 0):
+            row = {}
+            for ns in P["DRIFT_NS"]:
+                ch = pkg.Chain(pkg.make_params(L=cfg["L"], beta=cfg["beta"], dtau=cfg["dtau"], U=cfg["U"],
+                                               n_delay=cfg["n_delay"], n_stab=ns, seed=77, precision=prec))
+                ch.sweep(1)
+                row[ns] = ch.sweep(1).max_stab_drift
+                ch.close()
+            drift[key][{3: "tf32", 0: "fp64"}[prec]] = row
+    t_drift = time.perf_counter() - t0
+    clocks = ClockSampler(0)
+    clocks.start()
+    t1 = time.perf_counter()
+    comp = {"L12": precision_comparison(pkg, P["L12"], 1200)}
+    if args.steps > 0:
+        comp["L24"] = precision_comparison(pkg, P["L24"], 2400)
+    t_comp = time.perf_counter() - t1
+    ck = clocks.stop()
+    out = {"metric": "split-TF32 flush vs FP64: drift and equilibrium observables (difference +- sigma)",
+           "value": max(abs(v["z"]) for c in comp.values() for v in c[0].values()), "unit": "max |z|",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+           "dtype": "f64 vs f64 with tf32x3 flush", "data": "synthetic (random initial fields)",
+           "config": {"workload": "precision", "study": {k: v for k, v in P.items()}},
+           "drift_max_abs_vs_n_stab": drift, "drift_s": t_drift,
+           "comparison": {k: {"observables": v[0], "max_stab_drift": v[1]} for k, v in comp.items()},
+           "comparison_s": t_comp}
+    if ck:
+        out["clocks"] = ck
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -726,6 +811,8 @@ def main():
         run_batched(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_ours(args)
 

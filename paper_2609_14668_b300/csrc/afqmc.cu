@@ -349,8 +349,31 @@ void lu(afqmc_handle* h, double* At) {
 }
 
 int warp_grid(int ncols) { return (ncols * 32 + 255) / 256; }
-int cpb_grid(int ncols) { return (ncols + CPB - 1) / CPB; }
-size_t cpb_smem(int n) { return sizeof(double) * (size_t)(CPB + 2) * n; }
+// shape of the column-parallel kernels for matrix dimension n: <8 columns per
+// CTA, 8 prefetch registers> up to n = 2048, <4, 16> up to COL_MAX_N
+bool col_small(int n) { return n <= 2048; }
+int col_cpb(int n) { return col_small(n) ? 8 : 4; }
+int cpb_grid(int ncols, int n) { return (ncols + col_cpb(n) - 1) / col_cpb(n); }
+size_t cpb_smem(int n) { return sizeof(double) * (size_t)(col_cpb(n) + 2) * n; }
+
+void launch_form_q(afqmc_handle* h, const double* Vt, const double* tau, const double* sgn, double* Qt, int n) {
+    Scope sc(h, AFQMC_K_QRAUX);
+    if (col_small(n)) k_form_q<8, 8><<<cpb_grid(n, n), 256, cpb_smem(n), h->stream>>>(Vt, tau, sgn, Qt, n);
+    else k_form_q<4, 16><<<cpb_grid(n, n), 256, cpb_smem(n), h->stream>>>(Vt, tau, sgn, Qt, n);
+    CK(cudaGetLastError());
+}
+void launch_fwdsolve(afqmc_handle* h, const double* Lt, const int* piv, double* Yt, int n) {
+    Scope sc(h, AFQMC_K_QRAUX);
+    if (col_small(n)) k_fwdsolve_perm<8, 8><<<cpb_grid(n, n), 256, cpb_smem(n), h->stream>>>(Lt, piv, Yt, n, n);
+    else k_fwdsolve_perm<4, 16><<<cpb_grid(n, n), 256, cpb_smem(n), h->stream>>>(Lt, piv, Yt, n, n);
+    CK(cudaGetLastError());
+}
+void launch_backsolve(afqmc_handle* h, const double* Rt, const double* Yt, double* Xt, int n, const double* xs) {
+    Scope sc(h, AFQMC_K_QRAUX);
+    if (col_small(n)) k_backsolve<8, 8><<<cpb_grid(n, n), 256, cpb_smem(n), h->stream>>>(Rt, Yt, Xt, n, n, xs, h->st);
+    else k_backsolve<4, 16><<<cpb_grid(n, n), 256, cpb_smem(n), h->stream>>>(Rt, Yt, Xt, n, n, xs, h->st);
+    CK(cudaGetLastError());
+}
 
 // dynamic shared memory of k_update_slice: window block (phase B) or flush tiles (phase F)
 size_t update_smem(int W, int nd, int precision, int N = AFQMC_NOALLOC_MAX_N, int grid = 148) {
@@ -388,7 +411,7 @@ void udt_extend(afqmc_handle* h, const UDTe& in, const UDTe& out, int lo, int hi
     qr(h, AP);
     double* F = h->Wk[2];
     { Scope sc(h, AFQMC_K_QRAUX); k_make_F<<<n, 256, 0, h->stream>>>(AP, h->Dp, F, out.D, h->sgn, n, h->st); }
-    { Scope sc(h, AFQMC_K_QRAUX); k_form_q<<<cpb_grid(n), 256, cpb_smem(n), h->stream>>>(AP, h->tau, h->sgn, out.Ut, n); }
+    launch_form_q(h, AP, h->tau, h->sgn, out.Ut, n);
     double* Tp = h->Wk[3];
     { Scope sc(h, AFQMC_K_QRAUX); k_gather_rows<<<n, 256, 0, h->stream>>>(in.T, Tp, h->perm, nullptr, nullptr, n); }
     CK(cudaGetLastError());
@@ -416,10 +439,9 @@ void form_green(afqmc_handle* h, const UDTe& R, const UDTe& Lt, double* Gout, do
         Scope sc(h, AFQMC_K_QRAUX);
         k_transpose_scale<<<g, b, 0, h->stream>>>(R.Ut, Yt, n, n, h->DbR, 1, nullptr, 0);
     }
-    { Scope sc(h, AFQMC_K_QRAUX); k_fwdsolve_perm<<<cpb_grid(n), 256, cpb_smem(n), h->stream>>>(Mt, h->piv, Yt, n, n); }
+    launch_fwdsolve(h, Mt, h->piv, Yt, n);
     double* Wt = h->Wk[2];
-    { Scope sc(h, AFQMC_K_QRAUX); k_backsolve<<<cpb_grid(n), 256, cpb_smem(n), h->stream>>>(Mt, Yt, Wt, n, n, h->DbL, h->st); }
-    CK(cudaGetLastError());
+    launch_backsolve(h, Mt, Yt, Wt, n, h->DbL);
     gemm(h, Lt.Ut, 1, Wt, 1, Gout, 1.0, 0.0, nullptr, 0, nullptr, 0);
     const size_t nn = (size_t)n * n;
     if (G0t) {
@@ -434,9 +456,8 @@ void form_green(afqmc_handle* h, const UDTe& R, const UDTe& Lt, double* Gout, do
             Scope sc(h, AFQMC_K_QRAUX);
             k_transpose_scale<<<g, b, 0, h->stream>>>(R.T, Yt, n, n, h->DsR, 0, nullptr, 0);
         }
-        { Scope sc(h, AFQMC_K_QRAUX); k_fwdsolve_perm<<<cpb_grid(n), 256, cpb_smem(n), h->stream>>>(Mt, h->piv, Yt, n, n); }
-        { Scope sc(h, AFQMC_K_QRAUX); k_backsolve<<<cpb_grid(n), 256, cpb_smem(n), h->stream>>>(Mt, Yt, Wt, n, n, h->DbL, h->st); }
-        CK(cudaGetLastError());
+        launch_fwdsolve(h, Mt, h->piv, Yt, n);
+        launch_backsolve(h, Mt, Yt, Wt, n, h->DbL);
         gemm(h, Lt.Ut, 1, Wt, 1, Gt0, 1.0, 0.0, nullptr, 0, nullptr, 0);
     }
 }
@@ -845,10 +866,18 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         h->rowop_smem = sizeof(double2) * 2 * (size_t)h->vp * Np;
         if (h->rowop_smem > 200 * 1024) throw CudaFail{AFQMC_E_INVALID, "lattice too large for the row kernel"};
         CK(raise_smem_limit((const void*)k_rowop, h->rowop_smem));
-        if (N > PRE * 256) throw CudaFail{AFQMC_E_INVALID, "lattice too large for the column kernels"};
-        for (const void* f : {(const void*)k_apply_qt, (const void*)k_form_q, (const void*)k_backsolve,
-                              (const void*)k_fwdsolve_perm})
-            CK(raise_smem_limit(f, cpb_smem(N)));
+        if (N > COL_MAX_N)
+            throw CudaFail{AFQMC_E_INVALID, "matrix dimension " + std::to_string(N) + " above the column kernels' " +
+                                                std::to_string(COL_MAX_N) + " (2 L1 L2, doubled with a twist or the charge channel)"};
+        if (col_small(N)) {
+            for (const void* f : {(const void*)k_form_q<8, 8>, (const void*)k_backsolve<8, 8>,
+                                  (const void*)k_fwdsolve_perm<8, 8>})
+                CK(raise_smem_limit(f, cpb_smem(N)));
+        } else {
+            for (const void* f : {(const void*)k_form_q<4, 16>, (const void*)k_backsolve<4, 16>,
+                                  (const void*)k_fwdsolve_perm<4, 16>})
+                CK(raise_smem_limit(f, cpb_smem(N)));
+        }
         h->upd_grid = P.update_ctas > 0 ? P.update_ctas : h->sms;
         const size_t usmem = update_smem(h->W, h->nd, P.precision, N, h->upd_grid);
         CK(raise_smem_limit(upd_kernel(h->charge), usmem));
@@ -886,8 +915,8 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         h->sgn = h->dalloc<double>(N);
         h->tau = h->dalloc<double>(N);
         if (P.precision & 2) {
-            // the 32-bit class sums of the product kernel hold every exact window of K <= 2048
-            static_assert(((PRE * 256 + OZ_KC * OZ_WIN - 1) / (OZ_KC * OZ_WIN)) * (1ll << 24) < (1ll << 31),
+            // the 32-bit class sums of the product kernel hold every exact window of K <= COL_MAX_N
+            static_assert(((COL_MAX_N + OZ_KC * OZ_WIN - 1) / (OZ_KC * OZ_WIN)) * (1ll << 24) < (1ll << 31),
                           "class sums of the largest lattice overflow 32 bits");
             h->ozKpad = (N + OZ_KC - 1) / OZ_KC * OZ_KC;
             h->ozA = h->dalloc<__nv_bfloat16>((size_t)OZ_S * N * h->ozKpad);

@@ -11,7 +11,7 @@
 //     cyclically by CTAs, reflector j published through a flag and applied by
 //     every CTA to its own columns (one-column lookahead on the critical path);
 //   * column-parallel kernels (one warp per column, no inter-CTA sync) for
-//     applying the reflectors, forming Q and back substitution.
+//     forming Q and the triangular solves.
 // Matrices are row-major; a "column-major" matrix X is stored as its
 // transpose Xt (row c of Xt = column c of X).
 #pragma once
@@ -235,13 +235,16 @@ __global__ void __launch_bounds__(256) k_qr_cols(QRArgs q, int cols_in_smem) {
 }
 
 // ---------------------------------------------------------------------------
-// Column-parallel kernels on 8 columns per CTA (one warp each).  The 8 columns
-// stay in shared memory; the vector every column needs at step j (reflector
-// v_j, or column i of R) is staged once per step in shared memory for all 8
-// warps, with the next step's vector prefetched into registers while the
-// current step computes.  Dynamic shared memory: (CPB + 2) * n doubles.
+// Column-parallel kernels on CPB_ columns per CTA (one warp each, 256 threads).
+// The CPB_ columns stay in shared memory; the vector every column needs at
+// step j (reflector v_j, or column i of R) is staged once per step in shared
+// memory for all warps, with the next step's vector prefetched into registers
+// (PRE_ per thread, so n <= 256 PRE_) while the current step computes.
+// Dynamic shared memory: (CPB_ + 2) * n doubles.  Two shapes: <8, 8> for
+// n <= 2048, and <4, 16> for n <= 4096 (the larger matrices leave room in
+// shared memory for only four columns; the other four warps help staging).
 // ---------------------------------------------------------------------------
-constexpr int CPB = 8;    // columns per CTA
+constexpr int COL_MAX_N = 4096;   // largest matrix dimension of the column kernels
 
 __device__ __forceinline__ double dot4(const double* __restrict__ a, const double* __restrict__ b, int lo, int hi) {
     const int lane = threadIdx.x & 31;
@@ -259,18 +262,18 @@ __device__ __forceinline__ double dot4(const double* __restrict__ a, const doubl
 
 // Stage vector src[lo..hi) into dst[lo..hi) (whole CTA), using per-thread
 // prefetch registers: pre[q] holds src[lo + threadIdx.x + q*blockDim.x].
-constexpr int PRE = 8;   // supports n <= PRE * blockDim.x = 2048
-
-__device__ __forceinline__ void prefetch_vec(const double* __restrict__ src, int lo, int hi, double (&pre)[PRE]) {
+template <int PRE_>
+__device__ __forceinline__ void prefetch_vec(const double* __restrict__ src, int lo, int hi, double (&pre)[PRE_]) {
 #pragma unroll
-    for (int q = 0; q < PRE; ++q) {
+    for (int q = 0; q < PRE_; ++q) {
         const int i = lo + threadIdx.x + q * blockDim.x;
         pre[q] = (i < hi) ? __ldg(src + i) : 0.0;
     }
 }
-__device__ __forceinline__ void store_vec(double* dst, int lo, int hi, const double (&pre)[PRE]) {
+template <int PRE_>
+__device__ __forceinline__ void store_vec(double* dst, int lo, int hi, const double (&pre)[PRE_]) {
 #pragma unroll
-    for (int q = 0; q < PRE; ++q) {
+    for (int q = 0; q < PRE_; ++q) {
         const int i = lo + threadIdx.x + q * blockDim.x;
         if (i < hi) dst[i] = pre[q];
     }
@@ -416,28 +419,29 @@ __global__ void __launch_bounds__(256) k_lu_cols(LUArgs q, int cols_in_smem) {
 // Y <- (L_{n-2} P_{n-2} ... L_0 P_0) Y for every column y (row of
 // Yt): at step j the swap of rows j and piv[j], then elimination with column j
 // of the unit lower triangle of the column-major Lt, as stored at step j.
-// 8 columns per CTA in shared memory, column j of L staged once per step and
+// CPB_ columns per CTA in shared memory, column j of L staged once per step and
 // prefetched one step ahead, the pivot list staged in shared memory.
+template <int CPB_, int PRE_>
 __global__ void __launch_bounds__(256) k_fwdsolve_perm(const double* __restrict__ Lt, const int* __restrict__ piv,
                                                        double* Yt, int n, int ncols) {
     extern __shared__ double cs_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c0 = blockIdx.x * CPB;
+    const int c0 = blockIdx.x * CPB_;
     double* lbuf = cs_smem;
-    double* y = cs_smem + n + (size_t)warp * n;
-    int* spiv = reinterpret_cast<int*>(cs_smem + (size_t)(CPB + 1) * n);
+    double* y = cs_smem + n + (size_t)(warp < CPB_ ? warp : 0) * n;
+    int* spiv = reinterpret_cast<int*>(cs_smem + (size_t)(CPB_ + 1) * n);
     const int c = c0 + warp;
-    const bool has = c < ncols;
+    const bool has = warp < CPB_ && c < ncols;
     if (has)
         for (int i = lane; i < n; i += 32) y[i] = Yt[(size_t)c * n + i];
     for (int i = threadIdx.x; i < n; i += blockDim.x) spiv[i] = piv[i];
-    double pre[PRE];
-    prefetch_vec(Lt, 1, n, pre);
+    double pre[PRE_];
+    prefetch_vec<PRE_>(Lt, 1, n, pre);
     for (int j = 0; j < n - 1; ++j) {
         __syncthreads();
-        store_vec(lbuf, j + 1, n, pre);
+        store_vec<PRE_>(lbuf, j + 1, n, pre);
         __syncthreads();
-        if (j + 1 < n - 1) prefetch_vec(Lt + (size_t)(j + 1) * n, j + 2, n, pre);
+        if (j + 1 < n - 1) prefetch_vec<PRE_>(Lt + (size_t)(j + 1) * n, j + 2, n, pre);
         if (has) {
             // step j of P A = L U: swap rows j and piv[j], then eliminate with column j of L
             double yj = 0.0;
@@ -457,64 +461,33 @@ __global__ void __launch_bounds__(256) k_fwdsolve_perm(const double* __restrict_
         for (int i = lane; i < n; i += 32) Yt[(size_t)c * n + i] = y[i];
 }
 
-// Apply Q^T = H_{n-2} ... H_0 (H_0 first) to every column of Y (Yt rows).
-__global__ void __launch_bounds__(256) k_apply_qt(const double* __restrict__ Vt, const double* __restrict__ tau,
-                                                  double* Yt, int n, int ncols) {
-    extern __shared__ double cs_smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c0 = blockIdx.x * CPB;
-    double* vbuf = cs_smem;                      // n
-    double* col = cs_smem + n + (size_t)warp * n;
-    const int c = c0 + warp;
-    const bool has = c < ncols;
-    for (int w = 0; w < CPB; ++w)
-        if (c0 + w < ncols)
-            for (int i = threadIdx.x; i < n; i += blockDim.x) cs_smem[n + (size_t)w * n + i] = Yt[(size_t)(c0 + w) * n + i];
-    double pre[PRE];
-    prefetch_vec(Vt, 1, n, pre);                 // v_0 below the diagonal
-    for (int j = 0; j < n - 1; ++j) {
-        __syncthreads();
-        store_vec(vbuf, j + 1, n, pre);
-        if (threadIdx.x == 0) vbuf[j] = 1.0;
-        __syncthreads();
-        if (j + 1 < n - 1) prefetch_vec(Vt + (size_t)(j + 1) * n, j + 2, n, pre);
-        const double tj = __ldg(tau + j);
-        if (has && tj != 0.0) {
-            const double w = dot4(vbuf, col, j, n) * tj;
-            for (int i = j + lane; i < n; i += 32) col[i] = fma(-w, vbuf[i], col[i]);
-        }
-    }
-    __syncthreads();
-    for (int w = 0; w < CPB; ++w)
-        if (c0 + w < ncols)
-            for (int i = threadIdx.x; i < n; i += blockDim.x) Yt[(size_t)(c0 + w) * n + i] = cs_smem[n + (size_t)w * n + i];
-}
-
 // Form columns of Q = H_0 ... H_{n-2} (Qt rows), each multiplied by sgn[c]:
 // column c starts as e_c and takes H_j for j = min(c, n-2) down to 0.  Column c
 // needs about 2 c n FMAs, so the columns of a CTA are taken cyclically
 // (b, b + G, b + 2G, ...) to give every CTA the same mix of short and long ones.
+template <int CPB_, int PRE_>
 __global__ void __launch_bounds__(256) k_form_q(const double* __restrict__ Vt, const double* __restrict__ tau,
                                                 const double* __restrict__ sgn, double* Qt, int n) {
     extern __shared__ double cs_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double* vbuf = cs_smem;
-    double* col = cs_smem + n + (size_t)warp * n;
+    double* col = cs_smem + n + (size_t)(warp < CPB_ ? warp : 0) * n;
     const int c = blockIdx.x + gridDim.x * warp;
-    const bool has = c < n;
-    for (int i = lane; i < n; i += 32) col[i] = (i == c) ? 1.0 : 0.0;
+    const bool has = warp < CPB_ && c < n;
+    if (warp < CPB_)
+        for (int i = lane; i < n; i += 32) col[i] = (i == c) ? 1.0 : 0.0;
     int cmax = blockIdx.x;
-    for (int w = 1; w < CPB; ++w)
+    for (int w = 1; w < CPB_; ++w)
         if ((int)blockIdx.x + (int)gridDim.x * w < n) cmax = blockIdx.x + gridDim.x * w;
     const int jtop = min(cmax, n - 2);
-    double pre[PRE];
-    if (jtop >= 0) prefetch_vec(Vt + (size_t)jtop * n, jtop + 1, n, pre);
+    double pre[PRE_];
+    if (jtop >= 0) prefetch_vec<PRE_>(Vt + (size_t)jtop * n, jtop + 1, n, pre);
     for (int j = jtop; j >= 0; --j) {
         __syncthreads();
-        store_vec(vbuf, j + 1, n, pre);
+        store_vec<PRE_>(vbuf, j + 1, n, pre);
         if (threadIdx.x == 0) vbuf[j] = 1.0;
         __syncthreads();
-        if (j > 0) prefetch_vec(Vt + (size_t)(j - 1) * n, j, n, pre);
+        if (j > 0) prefetch_vec<PRE_>(Vt + (size_t)(j - 1) * n, j, n, pre);
         const double tj = __ldg(tau + j);
         if (has && j <= c && tj != 0.0) {
             const double w = dot4(vbuf, col, j, n) * tj;
@@ -531,26 +504,27 @@ __global__ void __launch_bounds__(256) k_form_q(const double* __restrict__ Vt, c
 // Back substitution: for every column y (row of Yt), solve R x = y with R the
 // upper triangle of the column-major Rt (R[i][c] = Rt[c][i]); writes
 // x_i * (xs ? 1/xs[i] : 1) into Xt.
+template <int CPB_, int PRE_>
 __global__ void __launch_bounds__(256) k_backsolve(const double* __restrict__ Rt, const double* __restrict__ Yt,
                                                    double* Xt, int n, int ncols, const double* xs, DevStatus* st) {
     extern __shared__ double cs_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c0 = blockIdx.x * CPB;
+    const int c0 = blockIdx.x * CPB_;
     double* rbuf = cs_smem;                      // column i of R, rows 0..i
-    double* x = cs_smem + n + (size_t)warp * n;
-    double* rinv = cs_smem + (size_t)(CPB + 1) * n;   // 1 / R_ii
+    double* x = cs_smem + n + (size_t)(warp < CPB_ ? warp : 0) * n;
+    double* rinv = cs_smem + (size_t)(CPB_ + 1) * n;   // 1 / R_ii
     const int c = c0 + warp;
-    const bool has = c < ncols;
+    const bool has = warp < CPB_ && c < ncols;
     for (int i = threadIdx.x; i < n; i += blockDim.x) rinv[i] = 1.0 / __ldg(Rt + (size_t)i * n + i);
     if (has)
         for (int i = lane; i < n; i += 32) x[i] = Yt[(size_t)c * n + i];
-    double pre[PRE];
-    prefetch_vec(Rt + (size_t)(n - 1) * n, 0, n, pre);
+    double pre[PRE_];
+    prefetch_vec<PRE_>(Rt + (size_t)(n - 1) * n, 0, n, pre);
     for (int i = n - 1; i >= 0; --i) {
         __syncthreads();
-        store_vec(rbuf, 0, i + 1, pre);
+        store_vec<PRE_>(rbuf, 0, i + 1, pre);
         __syncthreads();
-        if (i > 0) prefetch_vec(Rt + (size_t)(i - 1) * n, 0, i, pre);
+        if (i > 0) prefetch_vec<PRE_>(Rt + (size_t)(i - 1) * n, 0, i, pre);
         if (has) {
             const double xi = x[i] * rinv[i];
             __syncwarp();

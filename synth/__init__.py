@@ -44,6 +44,17 @@ LEARNED = dict(L=6, beta=6.0, dtau=0.1, U=3.73, n_delay=32, n_stab=10, b=2, T=2,
                n_cfg=600, train_steps=2000, batch=256, lr=3e-3)
 
 
+# Reduced-precision study: the split-TF32 flush (precision 3: with the
+# FP64-accurate tensor-core stabilisation products) against plain FP64
+# (precision 0), independent seeds, equilibrium averages at L = 12, beta t = 12
+# (and the headline L = 24 lattice); the drift profile uses n_stab in DRIFT_NS.
+PRECISION_STUDY = dict(L12=dict(L=12, beta=12.0, dtau=0.1, U=3.73, n_delay=32, n_stab=8, chains=16, warm=60,
+                                meas=200),
+                       L24=dict(L=24, beta=24.0, dtau=0.1, U=3.73, n_delay=64, n_stab=8, chains=4, warm=30,
+                                meas=30),
+                       DRIFT_NS=(1, 2, 4, 8))
+
+
 def batched_chains(twists=None):
     """(L, beta, theta, replica) of every chain of the batched workload.  twists:
     an explicit list of g*g twist angle pairs (e.g. a quasi-random sequence)

@@ -69,3 +69,36 @@ def test_tf32_chain_vs_fp64_chain(pkg):
     assert rel_err(G1, G0) < 1e-10      # same field: the recomputed G is FP64 in both modes
     for ch in chains:
         ch.close()
+
+
+def test_tf32_equilibrium_matches_fp64_within_two_sigma(pkg):
+    """Independent chains at L = 6, beta t = 6: 16 with the split-TF32 flush
+    (and the FP64-accurate tensor-core stabilisation products, precision 3),
+    16 plain FP64, 40 warm-up and 200 measured sweeps each.  The mean of the
+    chain means of e, D and S_AF must agree within 2 combined standard errors
+    (the chains are independent, so their spread carries the autocorrelation)."""
+    w = WORKLOADS["L6_beta6"]
+    C, warm, meas = 16, 40, 200
+    plist = [pkg.make_params(L=w["L"], beta=w["beta"], dtau=w["dtau"], U=w["U"], n_delay=w["n_delay"],
+                             n_stab=w["n_stab"], seed=600 + p, chain=c, measure=1, precision=p)
+             for p in (3, 0) for c in range(C)]
+    batch = pkg.Batch(plist)
+    batch.sweep(warm)
+    for c in batch.chains:
+        c.observables()
+    keys = ("energy", "double_occ", "S_af")
+    sums = np.zeros((2 * C, len(keys)))
+    for _ in range(meas):
+        batch.sweep(1)
+        for i, c in enumerate(batch.chains):
+            o = c.observables()
+            sums[i] += [o[k] for k in keys]
+    batch.close()
+    cm = sums / meas
+    for j, k in enumerate(keys):
+        a, b = cm[:C, j], cm[C:, j]
+        sd = np.hypot(a.std(ddof=1), b.std(ddof=1)) / np.sqrt(C)
+        z = (a.mean() - b.mean()) / sd
+        print(f"TF32_VS_FP64 L=6 {k}: tf32 {a.mean():.6f} fp64 {b.mean():.6f} diff {a.mean() - b.mean():+.2e} "
+              f"+- {sd:.1e} z = {z:+.2f}")
+        assert abs(z) < 2.0, (k, a.mean(), b.mean(), sd)
