@@ -36,16 +36,17 @@ FP64_PEAK_TFLOPS = 1.25      # nominal B300 FP64 rate (SIMT and tensor); DFMA mi
 
 
 def _tf32_peak():
-    # measured BF16 dense rate under the power cap (MEASURED_PEAKS.json, "sustained": the
-    # slice kernel is timed inside a seconds-long sweep) x nominal TF32/BF16 ratio 1.1/2.25;
-    # fallback: the recipe's sustained figure, 1.4 PFLOP/s
+    """TF32 dense peak = measured BF16 burst rate (MEASURED_PEAKS.json: cuBLAS bf16
+    GEMM timed alone, the way the roofline pass below times the slice kernel) x the
+    nominal TF32/BF16 ratio 1.1/2.25.  Fallback: the recipe's 1.8 PFLOP/s burst."""
     try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops_sustained"] * 1.1 / 2.25
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return pk["bf16_tflops"] * 1.1 / 2.25, "measured", pk.get("sm_max_mhz")
     except Exception:
-        return 1400.0 * 1.1 / 2.25
+        return 1800.0 * 1.1 / 2.25, "fallback", None
 
 
-TF32_PEAK_TFLOPS = _tf32_peak()
+TF32_PEAK_TFLOPS, TF32_PEAK_SOURCE, PEAK_SM_MHZ = _tf32_peak()
 
 
 def parse():
@@ -404,22 +405,38 @@ def captured_traffic(fam, precision, N):
     return nbytes
 
 
+def isolated_family_time(pkg, torch, chain, fam, dev):
+    """(launches, ms) of one kernel family over one sweep of a single chain with
+    nothing else running on the GPU: per-launch CUDA events on the chain's stream
+    then bracket the kernel alone, so their average is a kernel duration (with
+    several chains in flight the events of one stream also count the time other
+    chains' kernels hold the SMs)."""
+    torch.cuda.synchronize(dev)
+    pkg.afqmc_set_timing(chain.h, [fam])
+    chain.sweep(1)
+    t = pkg.afqmc_get_timing(chain.h)
+    pkg.afqmc_set_timing(chain.h, 0)
+    chain.observables()
+    return t[fam]
+
+
 def roofline_of(res, N, precision, cplx=False):
     """Roofline of the dominant kernel family: its algorithmic work per launch over
-    its average launch duration, timed with events in the timed region."""
-    timing, breakdown, fam, accepted = res["timing"], res["breakdown"], res["dominant"], res["accepted"]
+    its average launch duration, from the isolated single-chain pass."""
+    breakdown, fam, accepted = res["breakdown"], res["dominant"], res["accepted"]
     Nc = N // 2
-    nl, tms = timing[fam]
-    acc_per_update = accepted / max(timing["update"][0], 1)
+    nl, tms = res["isolated"]
+    acc_per_update = accepted / max(res["timing"]["update"][0], 1)
+    clocks = res.get("iso_clocks") or {}
     if fam == "update" and (precision & 1):
         # flush on the tensor cores: 2 N^2 algorithmic flops per accepted flip (x 4 for
         # complex G), each product done as three TF32 products (split-TF32), so the
         # peak is TF32 / 3
         fl = (4.0 if cplx else 1.0) * 2.0 * N * N * acc_per_update
         peak, bound, unit = TF32_PEAK_TFLOPS / 3.0, "tensor", "TFLOP/s"
-        note = ("split-TF32 peak = TF32 dense / 3; TF32 dense = measured BF16 sustained (the kernel "
-                "runs inside a seconds-long sweep) x nominal "
-                "TF32/BF16 ratio (1.1/2.25)")
+        note = (f"split-TF32 peak = TF32 dense / 3; TF32 dense = {TF32_PEAK_SOURCE} BF16 burst rate "
+                f"(the kernel is timed alone) x nominal TF32/BF16 ratio 1.1/2.25; peak measured at "
+                f"up to {PEAK_SM_MHZ} MHz SM clock")
     else:
         fl = algorithmic_flops(fam, N, Nc, acc_per_update, cplx)
         peak, bound, unit = FP64_PEAK_TFLOPS, "alu", "TFLOP/s"
@@ -427,8 +444,15 @@ def roofline_of(res, N, precision, cplx=False):
     if fl is None:
         return None
     ach = fl / (tms / nl / 1e3) / 1e12
+    cnl, ctms = res["timing"][fam]
     return {"bound": bound, "kernel": fam, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-            "traffic": None if cplx else captured_traffic(fam, precision, N), "peak_note": note, "flops_per_launch": fl, "avg_launch_ms": tms / nl,
+            "traffic": None if cplx else captured_traffic(fam, precision, N), "peak_note": note,
+            "flops_per_launch": fl, "avg_launch_ms": tms / nl, "launches_timed": nl,
+            "timing_note": ("CUDA events around each launch of the family during one extra sweep of one chain "
+                            "with no other chain running (after the timed region); the concurrent figure is "
+                            "the same events inside the timed region with every chain in flight"),
+            "concurrent_avg_launch_ms": ctms / max(cnl, 1),
+            "clocks_during_isolated_pass": clocks,
             "share_of_step": breakdown[fam][1] / sum(v[1] for v in breakdown.values()),
             "share_note": "share of device time in one breakdown sweep per chain with every launch timed"}
 
@@ -454,10 +478,16 @@ def run_ours(args):
     ref64 = None
     if args.precision != 0 and not args.no_fp64:
         ref64 = time_chain(pkg, torch, args, key, 0, rank, world, dev, dist, stream)
+        ref64["isolated"] = isolated_family_time(pkg, torch, ref64["chain"], ref64["dominant"], dev)
         for c in ref64["chains"]:
             c.close()
     ch = head["chain"]
     barrier = head["barrier"]
+    # the dominant family's kernel duration, timed alone (for the roofline)
+    iso_ck = ClockSampler(dev)
+    iso_ck.start()
+    head["isolated"] = isolated_family_time(pkg, torch, ch, head["dominant"], dev)
+    head["iso_clocks"] = iso_ck.stop()
 
     series = [[] for _ in head["chains"]]   # per-sweep observables of each chain
     # e2e: the public call a user makes per step (one sweep) plus reading the step's

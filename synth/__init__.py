@@ -26,6 +26,10 @@ WORKLOADS = {
     # column kernels (2N <= 2048), and the spin channel on the same lattice
     "L21_beta21_charge": dict(L=21, beta=21.0, dtau=0.1, U=3.73, n_delay=64, n_stab=7, hs_channel=1),
     "L21_beta21": dict(L=21, beta=21.0, dtau=0.1, U=3.73, n_delay=64, n_stab=7),
+    # the headline lattice with the charge-channel field (device embedding 2304 x 2304)
+    "L24_beta24_charge": dict(L=24, beta=24.0, dtau=0.1, U=3.73, n_delay=64, n_stab=8, hs_channel=1),
+    # the learned-proposal lattice: N = 3528 sites, M = 420 slices (G: 99.6 MB)
+    "L42_beta42": dict(L=42, beta=42.0, dtau=0.1, U=3.73, n_delay=64, n_stab=10),
 }
 
 

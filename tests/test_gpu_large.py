@@ -4,7 +4,8 @@ L = 24 lattice with complex G (twist, and the charge channel; the device holds
 the 2304 x 2304 real embedding).  For each: G at slice 0 recomputed from the
 QR-stabilised stacks, the first wrap, and one full slice update (same
 counter-based uniforms) against the FP64 CPU oracle; fields and accepted
-counts exactly, G to 1e-10 relative.  beta is kept short so that the dense
+counts exactly, G to 1e-10 relative (G at slice 0: or to twice the field's
+FP64 floor, where the conditioning puts that floor above 1e-10).  beta is kept short so that the dense
 oracle finishes in seconds; the GPU kernels are the same at any beta."""
 import numpy as np
 import pytest
@@ -35,18 +36,29 @@ _CACHE = {}
 
 def oracle_case(L, theta, hs, n_delay):
     """Field, G(0), the first wrap and one oracle slice update (cached: the
-    dense N = 3528 oracle takes tens of seconds)."""
+    dense N = 3528 oracle takes tens of seconds), and for the charge channel
+    the FP64 floor of G(0) for this field: the oracle's own deviation from the
+    direct inverse of 1 + B_M ... B_1 after one step of iterative refinement
+    (0 for the spin channel, whose G(0) is held to 1e-10 outright)."""
     key = (L, theta, hs, n_delay)
     if key not in _CACHE:
         from oracle.dqmc import Model, Chain
         m = Model(L, U=U, beta=BETA, dtau=DTAU, theta=theta, hs_channel=hs)
         f = random_field(m.M, m.N, 4200 + L + hs)
         G0 = m.green_stable(f, 0, NS)
+        floor = 0.0
+        if hs == 1:
+            # charge channel: e^{i alpha s} is unitary, so B_l has the condition
+            # number of e^{-dtau K} (~1.8) and the direct inverse is accurate
+            A = np.eye(m.N) + m.chain_product(f, 1, m.M)
+            Gd = np.linalg.inv(A)
+            Gd = Gd + Gd @ (np.eye(m.N) - A @ Gd)
+            floor = rel_err(G0, Gd)
         G1 = m.wrap(G0, f[0])
         oc = Chain(m, n_delay=n_delay, n_stab=NS, seed=SEED, field=f)
         oc.G = G1.copy()
         oc.update_slice(1, 0)
-        _CACHE[key] = (m.N, f, G0, G1, oc.G, oc.accepted, oc.field[0].copy())
+        _CACHE[key] = (m.N, f, G0, G1, oc.G, oc.accepted, oc.field[0].copy(), floor)
     return _CACHE[key]
 
 
@@ -57,12 +69,15 @@ def oracle_case(L, theta, hs, n_delay):
     (24, (0.0, 0.0), 1, 32, 2),
 ])
 def test_large_matrix_parity(pkg, L, theta, hs, n_delay, precision):
-    N, f, G0, G1, G_upd, n_upd, f_upd = oracle_case(L, theta, hs, n_delay)
+    N, f, G0, G1, G_upd, n_upd, f_upd, floor = oracle_case(L, theta, hs, n_delay)
     ch = pkg.Chain(pkg.make_params(L=L, beta=BETA, dtau=DTAU, U=U, n_delay=n_delay, n_stab=NS, seed=SEED,
                                    theta=theta, hs_channel=hs, precision=precision))
     assert ch.N == N
     ch.set_field(f)
-    assert rel_err(ch.green(0), G0) < TOL
+    # 1e-10 relative, unless the field's own FP64 floor is above it: the random
+    # charge-channel field at L = 24 has cond(1 + B_M...B_1) ~ 1.4e6 and |G| up
+    # to ~1e5, where the oracle itself is 9e-11 from the refined inverse
+    assert rel_err(ch.green(0), G0) < max(TOL, 2.0 * floor), floor
     assert rel_err(pkg.afqmc_wrap_matrix(ch.h, 1, +1, G0), G1) < 1e-12
     Gg, nacc = pkg.afqmc_update_slice(ch.h, 1, 0, 0, G1)
     assert nacc == n_upd > 0
