@@ -86,6 +86,8 @@ struct afqmc_handle {
     double* G = nullptr;
     double* Wk[6] = {};
     double *Xs = nullptr, *Ys = nullptr, *mcoef = nullptr, *xw = nullptr, *yw = nullptr, *Gw = nullptr;
+    uint32_t *tf_xh = nullptr, *tf_xl = nullptr, *tf_yh = nullptr, *tf_yl = nullptr;   // split-TF32 operands
+    int tf_ld = 0;
     int *msite = nullptr, *ctl = nullptr, *perm = nullptr;
     double *vtmp = nullptr, *Dp = nullptr, *sgn = nullptr, *tau = nullptr, *DbR = nullptr, *DsR = nullptr,
            *DbL = nullptr, *DsL = nullptr;
@@ -513,6 +515,7 @@ void update_slice(afqmc_handle* h, double* G, int l, int pass, int64_t sweep, co
     else a.ctr0 += (uint64_t)sweep * a.ctr_stride;
     a.n_acc = h->n_acc; a.st = h->st;
     a.precision = h->p.precision;
+    a.xh = h->tf_xh; a.xl = h->tf_xl; a.yh = h->tf_yh; a.yl = h->tf_yl; a.ldt = h->tf_ld;
     const size_t smem = update_smem(h->W, h->nd, h->p.precision, h->N, h->upd_grid);
     void* args[] = {&a};
     Scope sc(h, AFQMC_K_UPDATE);
@@ -903,6 +906,15 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         for (auto& w : h->Wk) w = h->dalloc<double>(nn);
         h->Xs = h->dalloc<double>((size_t)h->nd * N);
         h->Ys = h->dalloc<double>((size_t)h->nd * N);
+        if (P.precision & 1) {
+            // K-major TF32 parts of X and Y; rows padded to a multiple of 8 moves
+            // (the flush reads whole groups of 8 past the last pending move)
+            h->tf_ld = (h->nd + 7) & ~7;
+            for (uint32_t** t : {&h->tf_xh, &h->tf_xl, &h->tf_yh, &h->tf_yl}) {
+                *t = h->dalloc<uint32_t>((size_t)N * h->tf_ld);
+                CK(cudaMemset(*t, 0, sizeof(uint32_t) * (size_t)N * h->tf_ld));
+            }
+        }
         h->msite = h->dalloc<int>(h->nd);
         h->mcoef = h->dalloc<double>(h->nd);
         h->xw = h->dalloc<double>((size_t)h->nd * h->W);

@@ -50,30 +50,35 @@ __host__ __device__ __forceinline__ double sm64_uniform(uint64_t key, uint64_t n
 // Grid-wide barrier for cooperative launches.  Every CTA must call it.  The
 // wait is bounded by wait_limit(st); on timeout the error flag is set and the
 // function returns false, as it does when any CTA has flagged an error.
+// Thread 0 of a CTA arrives with an acquire-release add on the counter (it
+// publishes the CTA's writes, made visible to it by the bar.sync before); the
+// last one to arrive resets the counter and publishes the next generation with
+// a release store; the others poll the generation with acquire loads.
 __device__ __forceinline__ bool grid_barrier(DevStatus* st, int where) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int* vgen = &st->bar_gen;
-        unsigned int gen = *vgen;
-        __threadfence();
-        unsigned int arrived = atomicAdd(&st->bar_count, 1u);
+        unsigned int* cnt = &st->bar_count;
+        unsigned int* genp = &st->bar_gen;
+        unsigned int gen, arrived;
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(genp) : "memory");
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(cnt) : "memory");
         if (arrived == gridDim.x - 1) {
-            st->bar_count = 0;
-            __threadfence();
-            atomicAdd(&st->bar_gen, 1u);
+            asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" :: "l"(cnt), "r"(0u) : "memory");
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(genp), "r"(gen + 1u) : "memory");
         } else {
             const unsigned long long t0 = global_ns(), lim = wait_limit(st);
-            while (*vgen == gen) {
+            for (;;) {
+                unsigned int g;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(genp) : "memory");
+                if (g != gen) break;
                 if (*(volatile int*)&st->err) break;
                 if (global_ns() - t0 > lim) {
                     if (atomicCAS(&st->err, 0, DERR_TIMEOUT) == 0) st->where = where;
                     break;
                 }
-                __nanosleep(20);
             }
         }
-        __threadfence();
         s_ok = (*(volatile int*)&st->err) == 0;
     }
     __syncthreads();

@@ -123,6 +123,26 @@ struct QRArgs {
     DevStatus* st;
 };
 
+// dst[i - off] = src[i] for i in [lo, n) (whole CTA), through L2, with up to 8
+// loads per thread in flight before their stores: the copy of the published
+// column sits on the critical path of every column step.
+__device__ __forceinline__ void stage_column(const double* __restrict__ src, double* dst, int lo, int n, int off) {
+    constexpr int SB = 8;
+    for (int i0 = lo + threadIdx.x; i0 < n; i0 += SB * blockDim.x) {
+        double v[SB];
+#pragma unroll
+        for (int q = 0; q < SB; ++q) {
+            const int i = i0 + q * blockDim.x;
+            v[q] = i < n ? __ldcg(src + i) : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < SB; ++q) {
+            const int i = i0 + q * blockDim.x;
+            if (i < n) dst[i - off] = v[q];
+        }
+    }
+}
+
 // Publish column j (final: R entries above the diagonal, beta on it, the
 // reflector below) to global memory and raise flags[j].
 __device__ void qr_publish(const QRArgs& q, const double* col, int j, bool copy) {
@@ -215,8 +235,9 @@ __global__ void __launch_bounds__(256) k_qr_cols(QRArgs q, int cols_in_smem) {
         __syncthreads();
         if (s_abort) return;
         const double* colj = q.At + (size_t)j * n;
-        for (int i = j + threadIdx.x; i < n; i += blockDim.x) v[i - j] = (i == j) ? 1.0 : __ldcg(colj + i);
         const double tau = __ldcg(q.tau + j);
+        stage_column(colj, v, j + 1, n, j);
+        if (threadIdx.x == 0) v[0] = 1.0;
         __syncthreads();
         // lookahead: the owner of column j+1 finishes it first and publishes it
         if ((j + 1) % G == me) {
@@ -391,7 +412,7 @@ __global__ void __launch_bounds__(256) k_lu_cols(LUArgs q, int cols_in_smem) {
         if (s_abort) return;
         const int p = s_piv;
         const double* colj = q.At + (size_t)j * n;
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) l[i] = __ldcg(colj + i);
+        stage_column(colj, l, j + 1, n, 0);
         __syncthreads();
         // lookahead: the owner of column j+1 finishes it first and publishes it
         if ((j + 1) % G == me) {

@@ -63,6 +63,11 @@ struct UpdArgs {
     double* logR;
     double two_gamma;
     double dli_p, dli_m;          // Im Delta for s = +1, -1 (charge channel)
+    // split-TF32 flush (precision bit 0): the TF32 hi and lo parts of x_m(i) and
+    // y_m(i), written once by phase C, K-major: row i holds moves m = 0..ldt-1
+    // (ldt = n_delay rounded up to 4, so every row starts on 16 bytes)
+    uint32_t *xh, *xl, *yh, *yl;
+    int ldt;
 };
 
 // Window of the proposals.  Plain: positions t = 0..nw-1 are the sites c0 + t.
@@ -103,6 +108,14 @@ __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return r;
+}
+
+// x = hi + lo: hi the TF32 rounding of the FP32 rounding xf of x, lo the TF32
+// rounding of xf - hi
+__device__ __forceinline__ void split_tf32(double x, uint32_t& hi, uint32_t& lo) {
+    const float xf = (float)x;
+    hi = f32_to_tf32(xf);
+    lo = f32_to_tf32(xf - __uint_as_float(hi));
 }
 
 // ---------------------------------------------------------------------------
@@ -170,30 +183,44 @@ __device__ bool flush_tile_tcgen05(const UpdArgs& a, int k, int i0, int j0, unsi
         const int kp = (kc + 7) & ~7;
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-        constexpr int SB = 8;
-        for (int o0 = threadIdx.x; o0 < kp * TCT; o0 += SB * blockDim.x) {
-            double xv[SB], yv[SB];
+        // The operands were split into TF32 parts once, by phase C: copy groups
+        // of 4 moves (16 bytes) per row into the canonical layout, zero beyond
+        // the pending moves and beyond N.  Vector v -> (operand, group of 8 rows,
+        // group of 4 moves, row within the group) with the row fastest: a warp
+        // reads 8 rows x 64 contiguous bytes and stores 4 x 128 contiguous bytes
+        // of shared memory (no bank conflicts); all loads of a thread are issued
+        // before its stores.
+        const int groups = kp >> 2;                        // 4 moves per 16 bytes
+        const int total = 4 * TCT * groups;
+        constexpr int VB = 8;
+        for (int v0 = threadIdx.x; v0 < total; v0 += VB * blockDim.x) {
+            uint4 w[VB];
+            uint32_t off[VB];
 #pragma unroll
-            for (int q = 0; q < SB; ++q) {
-                const int o = o0 + q * blockDim.x;
-                const int m = o / TCT, r = o - m * TCT;
-                const bool in = o < kp * TCT && m < kc;
-                xv[q] = (in && i0 + r < N) ? __ldcg(a.Xs + (size_t)(k0 + m) * N + i0 + r) : 0.0;
-                yv[q] = (in && j0 + r < N) ? __ldcg(a.Ys + (size_t)(k0 + m) * N + j0 + r) : 0.0;
+            for (int q = 0; q < VB; ++q) {
+                const int v = v0 + q * blockDim.x;
+                w[q] = make_uint4(0u, 0u, 0u, 0u);
+                off[q] = 0xffffffffu;
+                if (v >= total) continue;
+                const int rl = v & 7;
+                const int t = v >> 3;
+                const int g4 = t % groups;
+                const int t2 = t / groups;
+                const int rg = t2 % (TCT / 8), op = t2 / (TCT / 8);   // 0 Ah, 1 Al, 2 Bh, 3 Bl
+                const int r = 8 * rg + rl, m = 4 * g4;
+                off[q] = (uint32_t)op * TCT * TCK * 4 + tc_off(r, m, kp);
+                const int gi = (op < 2 ? i0 : j0) + r;
+                if (gi < N && m < kc) {
+                    const uint32_t* src = op == 0 ? a.xh : op == 1 ? a.xl : op == 2 ? a.yh : a.yl;
+                    w[q] = __ldcg(reinterpret_cast<const uint4*>(src + (size_t)gi * a.ldt + k0 + m));
+                    if (m + 1 >= kc) w[q].y = 0u;
+                    if (m + 2 >= kc) w[q].z = 0u;
+                    if (m + 3 >= kc) w[q].w = 0u;
+                }
             }
 #pragma unroll
-            for (int q = 0; q < SB; ++q) {
-                const int o = o0 + q * blockDim.x;
-                if (o >= kp * TCT) break;
-                const int m = o / TCT, r = o - m * TCT;
-                const float xf = (float)xv[q], yf = (float)yv[q];
-                const uint32_t xhi = f32_to_tf32(xf), yhi = f32_to_tf32(yf);
-                const uint32_t off = tc_off(r, m, kp);
-                *reinterpret_cast<uint32_t*>(Ah + off) = xhi;
-                *reinterpret_cast<uint32_t*>(Al + off) = f32_to_tf32(xf - __uint_as_float(xhi));
-                *reinterpret_cast<uint32_t*>(Bh + off) = yhi;
-                *reinterpret_cast<uint32_t*>(Bl + off) = f32_to_tf32(yf - __uint_as_float(yhi));
-            }
+            for (int q = 0; q < VB; ++q)
+                if (off[q] != 0xffffffffu) *reinterpret_cast<uint4*>(sm + off[q]) = w[q];
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -242,20 +269,29 @@ __device__ bool flush_tile_tcgen05(const UpdArgs& a, int k, int i0, int j0, unsi
         for (int q = 0; q < 32; ++q) ct[row * CLD + cbase + cc + q] = __uint_as_float(v[q]);
     }
     __syncthreads();
-    for (int r = warp; r < TCT; r += 8) {
-        const int gi = i0 + r;
-        if (gi >= N) break;
-        double* grow = a.G + (size_t)gi * N + j0;
-        double gv[TCT / 32];
+    // G -= tile: each warp takes rows r, r + 8, ...; the loads of RB rows are in
+    // flight together before their subtractions and stores
+    constexpr int RB = 4;
+    for (int r0 = warp; r0 < TCT; r0 += 8 * RB) {
+        double gv[RB][TCT / 32];
 #pragma unroll
-        for (int q = 0; q < TCT / 32; ++q) {
-            const int c = lane + 32 * q;
-            gv[q] = (j0 + c < N) ? __ldcg(grow + c) : 0.0;
+        for (int b = 0; b < RB; ++b) {
+            const int gi = i0 + r0 + 8 * b;
+#pragma unroll
+            for (int q = 0; q < TCT / 32; ++q) {
+                const int c = lane + 32 * q;
+                gv[b][q] = (gi < N && j0 + c < N) ? __ldcg(a.G + (size_t)gi * N + j0 + c) : 0.0;
+            }
         }
 #pragma unroll
-        for (int q = 0; q < TCT / 32; ++q) {
-            const int c = lane + 32 * q;
-            if (j0 + c < N) grow[c] = gv[q] - (double)ct[r * CLD + c];
+        for (int b = 0; b < RB; ++b) {
+            const int r = r0 + 8 * b, gi = i0 + r;
+            if (gi >= N) break;
+#pragma unroll
+            for (int q = 0; q < TCT / 32; ++q) {
+                const int c = lane + 32 * q;
+                if (j0 + c < N) a.G[(size_t)gi * N + j0 + c] = gv[b][q] - (double)ct[r * CLD + c];
+            }
         }
     }
     return true;
@@ -307,10 +343,25 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
             __shared__ double s_c[2], s_c2[2];
             const int nw = win_len(a, cursor);
             const int ld = W + 1;
-            for (int o = threadIdx.x; o < nw * nw; o += blockDim.x) {
-                const int r = o / nw, c = o - r * nw;
-                Gw[r * ld + c] = (k == 0) ? __ldcg(a.G + (size_t)win_site(a, cursor, r) * N + win_site(a, cursor, c))
-                                          : __ldcg(a.Gw + r * W + c);
+            {
+                // W x W block: every load of a thread in flight before its stores
+                constexpr int BL = (UPD_WMAX * UPD_WMAX + UPD_THREADS - 1) / UPD_THREADS;
+                double v[BL];
+#pragma unroll
+                for (int q = 0; q < BL; ++q) {
+                    const int o = threadIdx.x + q * blockDim.x;
+                    v[q] = 0.0;
+                    if (o < nw * nw) {
+                        const int r = o / nw, c = o - r * nw;
+                        v[q] = (k == 0) ? __ldcg(a.G + (size_t)win_site(a, cursor, r) * N + win_site(a, cursor, c))
+                                        : __ldcg(a.Gw + r * W + c);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < BL; ++q) {
+                    const int o = threadIdx.x + q * blockDim.x;
+                    if (o < nw * nw) Gw[(o / nw) * ld + o % nw] = v[q];
+                }
             }
             for (int t = threadIdx.x; t < nw; t += blockDim.x) {
                 const int ps = win_phys(a, cursor, t);
@@ -330,6 +381,71 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
             __syncthreads();
             int kk = k, tstop = nw, t0 = 0, it = 0;
             double lacc = 0.0;                            // forced mode: sum of log R (thread 0)
+            if (CHARGE == 0 && !a.pair && !a.force) {
+                // Spin channel, real G: warp 0 holds window position q in lane q,
+                // with the current diagonal entry g, the ratio r = 1 + Delta (1 - g),
+                // its accept test and the coefficient Delta / r computed ahead of
+                // time.  A ballot over the positions not yet visited names the next
+                // accepted site at once, so no thread walks the rejected sites one
+                // by one; each value has the arithmetic of the serial scan below,
+                // so the decisions and the block are the same.
+                const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+                double g = 0.0, rq = 0.0, cq = 0.0;
+                bool okq = false;
+                auto refresh = [&](int q) {
+                    rq = fma(-dd[q], g, od[q]);
+                    if (!isfinite(rq)) { flag_error(a.st, DERR_NUMERIC, 200); okq = false; cq = 0.0; return; }
+                    okq = rq * rq > vv[q];
+                    cq = dd[q] * recip_nr(rq);
+                };
+                if (warp == 0 && lane < nw) { g = Gw[lane * ld + lane]; refresh(lane); }
+                for (;; ++it) {
+                    const int slot = it & 1;
+                    if (warp == 0) {
+                        const unsigned m = __ballot_sync(0xffffffffu, okq && lane >= t0 && lane < nw);
+                        const int tf = m ? __ffs((int)m) - 1 : -1;
+                        const double c = __shfl_sync(0xffffffffu, cq, tf >= 0 ? tf : 0);
+                        if (lane == 0) { s_found[slot] = tf; s_c[slot] = c; }
+                    }
+                    __syncthreads();
+                    const int tf = s_found[slot];
+                    if (tf < 0) break;
+                    const double c = s_c[slot];
+                    if (threadIdx.x == 32) {
+                        a.msite[kk] = cursor + tf;
+                        a.mcoef[kk] = c;
+                        a.s[cursor + tf] = (int8_t)(-sw[tf]);
+                    }
+                    const int rest = nw - tf - 1;
+                    for (int p = (int)threadIdx.x - 32; p >= 0 && p < rest; p += blockDim.x - 32) {
+                        const int q = tf + 1 + p;
+                        a.xw[kk * W + q] = c * Gw[q * ld + tf];
+                        a.yw[kk * W + q] = -Gw[tf * ld + q];
+                    }
+                    if (warp == 0) {
+                        // the diagonal of the later positions, then their tests
+                        if (lane > tf && lane < nw) {
+                            g = fma(c * Gw[lane * ld + tf], Gw[tf * ld + lane], g);
+                            refresh(lane);
+                        }
+                    } else if (warp != 4 && lane < rest) {
+                        // the off-diagonal trailing block (column and row tf are read
+                        // only): warps 1-3 and 5-7 take rows in turn, a lane takes a
+                        // column.  Warp 4 shares warp 0's sub-partition, whose FP64
+                        // unit carries the decision chain: it stays off FP64 here.
+                        const int pp = tf + 1 + lane;
+                        const double ytf = Gw[tf * ld + pp];
+                        const int wr = warp < 4 ? warp - 1 : warp - 2;      // 0..5
+                        for (int q = tf + 1 + wr; q < nw; q += 6) {
+                            if (q == pp) continue;
+                            Gw[q * ld + pp] = fma(c * Gw[q * ld + tf], ytf, Gw[q * ld + pp]);
+                        }
+                    }
+                    t0 = tf + 1;
+                    ++kk;
+                    if (kk == nd) { tstop = tf + 1; break; }
+                }
+            } else
             for (;; ++it) {
                 const int slot = it & 1;
                 if (threadIdx.x == 0) {
@@ -605,6 +721,15 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                 if (mine) {
                     a.Xs[(size_t)mm * N + j] = xv;
                     a.Ys[(size_t)mm * N + j] = yv;
+                    if (a.precision & 1) {
+                        uint32_t h, l;
+                        split_tf32(xv, h, l);
+                        a.xh[(size_t)j * a.ldt + mm] = h;
+                        a.xl[(size_t)j * a.ldt + mm] = l;
+                        split_tf32(yv, h, l);
+                        a.yh[(size_t)j * a.ldt + mm] = h;
+                        a.yl[(size_t)j * a.ldt + mm] = l;
+                    }
                 }
             }
         }
