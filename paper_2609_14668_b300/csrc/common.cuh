@@ -68,6 +68,8 @@ __device__ __forceinline__ bool grid_barrier(DevStatus* st, int where) {
             asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(genp), "r"(gen + 1u) : "memory");
         } else {
             const unsigned long long t0 = global_ns(), lim = wait_limit(st);
+            unsigned int nap = 32;     // back-off: the waiting CTAs poll one L2 line while
+                                       // the working ones need the memory system
             for (;;) {
                 unsigned int g;
                 asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(genp) : "memory");
@@ -77,6 +79,8 @@ __device__ __forceinline__ bool grid_barrier(DevStatus* st, int where) {
                     if (atomicCAS(&st->err, 0, DERR_TIMEOUT) == 0) st->where = where;
                     break;
                 }
+                __nanosleep(nap);
+                if (nap < 512) nap <<= 1;
             }
         }
         s_ok = (*(volatile int*)&st->err) == 0;

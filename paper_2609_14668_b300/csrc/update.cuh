@@ -89,6 +89,25 @@ __device__ __forceinline__ int win_phys(const UpdArgs& a, int c0, int t) {   // 
     return a.pair ? c0 + (t >> 1) : c0 + t;
 }
 
+// 1 / r from the hardware estimate y0 (relative error below 2^-19.9 on this
+// part, measured) by one cubic step y0 (1 + e + e^2), e = 1 - r y0: the error
+// e^3 < 2^-59 is below FP64 rounding, in three dependent FP64 operations
+__device__ __forceinline__ double recip_fast(double r) {
+    double y0;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(r));
+    const double e = fma(-r, y0, 1.0);
+    return fma(y0, fma(e, e, e), y0);
+}
+
+// |x| > t for t >= 0 (not NaN), on the bit patterns (non-negative doubles order
+// as their integer images): keeps the comparison off the FP64 unit
+__device__ __forceinline__ bool abs_gt(double x, double t) {
+    return (__double_as_longlong(x) & 0x7fffffffffffffffll) > __double_as_longlong(t);
+}
+__device__ __forceinline__ bool finite_bits(double x) {
+    return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
 // 1 / r: hardware reciprocal estimate refined by two Newton steps
 __device__ __forceinline__ double recip_nr(double r) {
     double y;
@@ -169,6 +188,8 @@ __device__ __forceinline__ uint32_t tc_off(int r, int m, int kp) {
 }
 
 constexpr int TCK = 32;                   // K staged per round (shared memory: 4 x 128 x 32 x 4 B = 64 KB)
+static_assert((TCK & (TCK / 4 - 1)) == 0 && ((TCK / 4) & (TCK / 4 - 1)) == 0 && ((TCT / 8) & (TCT / 8 - 1)) == 0,
+              "staging index arithmetic uses shifts");
 
 // returns false on a wait timeout (error flagged)
 __device__ bool flush_tile_tcgen05(const UpdArgs& a, int k, int i0, int j0, unsigned char* sm, uint32_t tmem,
@@ -180,7 +201,7 @@ __device__ bool flush_tile_tcgen05(const UpdArgs& a, int k, int i0, int j0, unsi
     unsigned char* Bl = sm + 3 * TCT * TCK * 4;
     for (int k0 = 0; k0 < k; k0 += TCK) {
         const int kc = min(TCK, k - k0);
-        const int kp = (kc + 7) & ~7;
+        const int kp = TCK;                                // full rounds: moves kc..31 are zero
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         // The operands were split into TF32 parts once, by phase C: copy groups
@@ -190,8 +211,8 @@ __device__ bool flush_tile_tcgen05(const UpdArgs& a, int k, int i0, int j0, unsi
         // reads 8 rows x 64 contiguous bytes and stores 4 x 128 contiguous bytes
         // of shared memory (no bank conflicts); all loads of a thread are issued
         // before its stores.
-        const int groups = kp >> 2;                        // 4 moves per 16 bytes
-        const int total = 4 * TCT * groups;
+        constexpr int groups = TCK / 4;                    // 4 moves per 16 bytes
+        constexpr int total = 4 * TCT * groups;
         constexpr int VB = 8;
         for (int v0 = threadIdx.x; v0 < total; v0 += VB * blockDim.x) {
             uint4 w[VB];
@@ -204,9 +225,9 @@ __device__ bool flush_tile_tcgen05(const UpdArgs& a, int k, int i0, int j0, unsi
                 if (v >= total) continue;
                 const int rl = v & 7;
                 const int t = v >> 3;
-                const int g4 = t % groups;
+                const int g4 = t & (groups - 1);
                 const int t2 = t / groups;
-                const int rg = t2 % (TCT / 8), op = t2 / (TCT / 8);   // 0 Ah, 1 Al, 2 Bh, 3 Bl
+                const int rg = t2 & (TCT / 8 - 1), op = t2 / (TCT / 8);   // 0 Ah, 1 Al, 2 Bh, 3 Bl
                 const int r = 8 * rg + rl, m = 4 * g4;
                 off[q] = (uint32_t)op * TCT * TCK * 4 + tc_off(r, m, kp);
                 const int gi = (op < 2 ? i0 : j0) + r;
@@ -300,7 +321,7 @@ __device__ bool flush_tile_tcgen05(const UpdArgs& a, int k, int i0, int j0, unsi
 // CHARGE = 1: charge-channel field (complex Delta, pair mode); a template
 // parameter so that the spin-channel kernel carries none of its code.
 template <int CHARGE>
-__global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
+__global__ void __launch_bounds__(UPD_THREADS, 1) k_update_slice(UpdArgs a) {
     extern __shared__ double upd_smem[];
     const int N = a.N, W = a.W, nd = a.nd;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -338,7 +359,8 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
             double* vv = Gw + W * (W + 1);                // W thresholds on r^2: u e^{-2 gamma s}
             double* dd = vv + W;                          // W values of Delta
             double* od = dd + W;                          // W values of 1 + Delta (charge: Im Delta)
-            int8_t* sw = reinterpret_cast<int8_t*>(od + W); // W field values
+            double* xs = od + W;                          // W: x of the current move at the window positions
+            int8_t* sw = reinterpret_cast<int8_t*>(xs + W); // W field values
             __shared__ int s_found[2];
             __shared__ double s_c[2], s_c2[2];
             const int nw = win_len(a, cursor);
@@ -389,16 +411,35 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                 // accepted site at once, so no thread walks the rejected sites one
                 // by one; each value has the arithmetic of the serial scan below,
                 // so the decisions and the block are the same.
+                // On this part every FP64 warp instruction holds its sub-partition's
+                // FP64 unit for ~64 cycles whatever the number of active lanes, so
+                // the decision chain is written with as few of them as possible:
+                // lane q keeps rr = r / Delta, which an accepted move at tf changes
+                // by -c G(q,tf) G(tf,q) (c = Delta / r of that move, the diagonal
+                // change times Delta); the test r^2 > v reads rr^2 > v / Delta^2 and
+                // the coefficient Delta / r of lane q is 1 / rr.  Delta = 0 (U = 0):
+                // r = 1 and c = 0.
                 const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-                double g = 0.0, rq = 0.0, cq = 0.0;
-                bool okq = false;
-                auto refresh = [&](int q) {
-                    rq = fma(-dd[q], g, od[q]);
-                    if (!isfinite(rq)) { flag_error(a.st, DERR_NUMERIC, 200); okq = false; cq = 0.0; return; }
-                    okq = rq * rq > vv[q];
-                    cq = dd[q] * recip_nr(rq);
+                double rr = 0.0, sq = 0.0, cq = 0.0;
+                bool okq = false, dz = false;
+                auto test = [&]() {     // r^2 > v  <=>  |rr| > sqrt(v) / |Delta| = sq
+                    if (dz) return;
+                    if (!finite_bits(rr)) { flag_error(a.st, DERR_NUMERIC, 200); okq = false; cq = 0.0; return; }
+                    okq = abs_gt(rr, sq);
+                    cq = recip_fast(rr);
                 };
-                if (warp == 0 && lane < nw) { g = Gw[lane * ld + lane]; refresh(lane); }
+                if (warp == 0 && lane < nw) {
+                    const double dq = dd[lane];
+                    dz = dq == 0.0;
+                    if (dz) {
+                        okq = 1.0 > vv[lane];
+                    } else {
+                        const double inv = 1.0 / dq;
+                        rr = fma(-dq, Gw[lane * ld + lane], od[lane]) * inv;
+                        sq = sqrt(vv[lane]) * fabs(inv);
+                        test();
+                    }
+                }
                 for (;; ++it) {
                     const int slot = it & 1;
                     if (warp == 0) {
@@ -411,34 +452,55 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_slice(UpdArgs a) {
                     const int tf = s_found[slot];
                     if (tf < 0) break;
                     const double c = s_c[slot];
-                    if (threadIdx.x == 32) {
-                        a.msite[kk] = cursor + tf;
-                        a.mcoef[kk] = c;
-                        a.s[cursor + tf] = (int8_t)(-sw[tf]);
-                    }
                     const int rest = nw - tf - 1;
-                    for (int p = (int)threadIdx.x - 32; p >= 0 && p < rest; p += blockDim.x - 32) {
-                        const int q = tf + 1 + p;
-                        a.xw[kk * W + q] = c * Gw[q * ld + tf];
-                        a.yw[kk * W + q] = -Gw[tf * ld + q];
-                    }
                     if (warp == 0) {
-                        // the diagonal of the later positions, then their tests
-                        if (lane > tf && lane < nw) {
-                            g = fma(c * Gw[lane * ld + tf], Gw[tf * ld + lane], g);
-                            refresh(lane);
+                        if (lane > tf && lane < nw && !dz) {
+                            rr = fma(-c, Gw[lane * ld + tf] * Gw[tf * ld + lane], rr);
+                            test();
                         }
-                    } else if (warp != 4 && lane < rest) {
-                        // the off-diagonal trailing block (column and row tf are read
-                        // only): warps 1-3 and 5-7 take rows in turn, a lane takes a
-                        // column.  Warp 4 shares warp 0's sub-partition, whose FP64
-                        // unit carries the decision chain: it stays off FP64 here.
-                        const int pp = tf + 1 + lane;
-                        const double ytf = Gw[tf * ld + pp];
-                        const int wr = warp < 4 ? warp - 1 : warp - 2;      // 0..5
-                        for (int q = tf + 1 + wr; q < nw; q += 6) {
-                            if (q == pp) continue;
-                            Gw[q * ld + pp] = fma(c * Gw[q * ld + tf], ytf, Gw[q * ld + pp]);
+                    } else {
+                        if (threadIdx.x == 32) {
+                            a.msite[kk] = cursor + tf;
+                            a.mcoef[kk] = c;
+                            a.s[cursor + tf] = (int8_t)(-sw[tf]);
+                        }
+                        // x and y of the move at the later window positions: to the
+                        // recursion of phase C (global) and to the trailing update
+                        for (int p = (int)threadIdx.x - 32; p < rest; p += blockDim.x - 32) {
+                            const int q = tf + 1 + p;
+                            const double xq = c * Gw[q * ld + tf];
+                            xs[q] = xq;
+                            a.xw[kk * W + q] = xq;
+                            a.yw[kk * W + q] = -Gw[tf * ld + q];
+                        }
+                        asm volatile("bar.sync 1, %0;" :: "r"(UPD_THREADS - 32) : "memory");
+                        if (warp != 4) {
+                            // the off-diagonal trailing block, G(q,p) += x_q G(tf,p) for
+                            // q, p > tf (column and row tf are read only), packed 32
+                            // entries per warp instruction over warps 1-3 and 5-7 (warp 4
+                            // shares warp 0's sub-partition and stays off FP64)
+                            const int wr = warp < 4 ? warp - 1 : warp - 2;      // 0..5
+                            const int tot = rest * rest;
+                            const float rinv = 1.0f / (float)max(rest, 1);
+                            // entry e -> (e / rest, e % rest); the FP32 quotient is off
+                            // by at most one for e < 1024 and is corrected
+                            auto split = [&](int e, int& q, int& pp) {
+                                int qi = __float2int_rz((float)e * rinv);
+                                if (qi * rest > e) --qi;
+                                else if ((qi + 1) * rest <= e) ++qi;
+                                q = tf + 1 + qi;
+                                pp = tf + 1 + (e - qi * rest);
+                            };
+                            for (int e0 = 32 * wr; e0 < tot; e0 += 2 * 6 * 32) {
+                                const int e1 = e0 + lane, e2 = e0 + 6 * 32 + lane;
+                                int q1 = 0, p1 = 0, q2 = 0, p2 = 0;
+                                const bool h1 = e1 < tot, h2 = e2 < tot;
+                                double x1 = 0.0, y1 = 0.0, g1 = 0.0, x2 = 0.0, y2 = 0.0, g2 = 0.0;
+                                if (h1) { split(e1, q1, p1); x1 = xs[q1]; y1 = Gw[tf * ld + p1]; g1 = Gw[q1 * ld + p1]; }
+                                if (h2) { split(e2, q2, p2); x2 = xs[q2]; y2 = Gw[tf * ld + p2]; g2 = Gw[q2 * ld + p2]; }
+                                if (h1 && q1 != p1) Gw[q1 * ld + p1] = fma(x1, y1, g1);
+                                if (h2 && q2 != p2) Gw[q2 * ld + p2] = fma(x2, y2, g2);
+                            }
                         }
                     }
                     t0 = tf + 1;
