@@ -73,7 +73,9 @@ struct afqmc_handle {
     bool own_stream = false;
     int sms = 0;
     int upd_grid = 0;              // CTAs of the cooperative slice kernel
-    // precision bit 1: digit planes and exponents of the Ozaki products
+    // precision bit 1: digit planes and exponents of the Ozaki products, and the
+    // tensor maps of the two digit-plane arrays (tensor-memory-access staging)
+    CUtensorMap oz_tmA{}, oz_tmB{};
     __nv_bfloat16 *ozA = nullptr, *ozB = nullptr;
     int *ozea = nullptr, *ozeb = nullptr;
     int ozKpad = 0;
@@ -277,6 +279,42 @@ DiagScale vdiag(afqmc_handle* h, int l, int spin_sign, int charge_sign) {
     return spin_sign > 0 ? DiagScale{s, h->egp, h->egm} : DiagScale{s, h->egm, h->egp};
 }
 
+// cuTensorMapEncodeTiled from the driver (through the runtime's entry-point query,
+// so the library needs no link against the driver library)
+using TensorMapEncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                       const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                       CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+std::mutex g_tmap_mutex;
+
+TensorMapEncodeFn tensor_map_encoder() {
+    static TensorMapEncodeFn fn = nullptr;
+    std::lock_guard<std::mutex> lock(g_tmap_mutex);
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<TensorMapEncodeFn>(ptr);
+    }
+    return fn;
+}
+
+// 3-D tensor map (k, row, digit) of OZ_S BF16 digit planes [digit][row][Kpad],
+// box 8 x box_rows x OZ_S: one copy stages 8 values of k of all digits of a tile
+void encode_digit_planes(CUtensorMap* map, void* base, int rows, int Kpad, int box_rows) {
+    TensorMapEncodeFn enc = tensor_map_encoder();
+    if (!enc) throw CudaFail{AFQMC_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver"};
+    const cuuint64_t dims[3] = {(cuuint64_t)Kpad, (cuuint64_t)rows, (cuuint64_t)OZ_S};
+    const cuuint64_t strides[2] = {(cuuint64_t)Kpad * 2, (cuuint64_t)rows * Kpad * 2};
+    const cuuint32_t box[3] = {8, (cuuint32_t)box_rows, (cuuint32_t)OZ_S};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw CudaFail{AFQMC_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r)};
+}
+
 // C = alpha rs .* (op(A) op(B)) .* cs + beta C on the BF16 tensor cores, FP64-accurate (ozaki.cuh)
 void gemm_oz(afqmc_handle* h, const double* A, int transA, const double* B, int transB, double* C, double alpha,
              double beta, const double* rs, int rs_inv, const double* cs, int cs_inv) {
@@ -299,7 +337,7 @@ void gemm_oz(afqmc_handle* h, const double* A, int transA, const double* B, int 
     OzArgs g{h->ozA, h->ozB, h->ozea, h->ozeb, n, n, Kp, C, n, alpha, beta, rs, cs, rs_inv, cs_inv, h->st};
     dim3 grid((n + OZ_TN - 1) / OZ_TN, (n + OZ_TM - 1) / OZ_TM);
     Scope sc(h, AFQMC_K_GEMM);
-    k_oz_gemm<<<grid, OZ_THREADS, oz_smem_bytes(), h->stream>>>(g);
+    k_oz_gemm<<<grid, OZ_THREADS, oz_smem_bytes(), h->stream>>>(h->oz_tmA, h->oz_tmB, g);
     CK(cudaGetLastError());
 }
 
@@ -927,14 +965,17 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         h->sgn = h->dalloc<double>(N);
         h->tau = h->dalloc<double>(N);
         if (P.precision & 2) {
-            // the 32-bit class sums of the product kernel hold every exact window of K <= COL_MAX_N
-            static_assert(((COL_MAX_N + OZ_KC * OZ_WIN - 1) / (OZ_KC * OZ_WIN)) * (1ll << 24) < (1ll << 31),
-                          "class sums of the largest lattice overflow 32 bits");
+            // the 64-bit integer sum of classes 0..3 of the product kernel adds below 2^46 per
+            // exact window of K and must stay exact in FP64 (2^53) for K <= COL_MAX_N
+            static_assert(((COL_MAX_N + OZ_KC * OZ_WIN - 1) / (OZ_KC * OZ_WIN)) * (1ll << 46) <= (1ll << 53),
+                          "class sums of the largest lattice exceed 2^53");
             h->ozKpad = (N + OZ_KC - 1) / OZ_KC * OZ_KC;
             h->ozA = h->dalloc<__nv_bfloat16>((size_t)OZ_S * N * h->ozKpad);
             h->ozB = h->dalloc<__nv_bfloat16>((size_t)OZ_S * N * h->ozKpad);
             h->ozea = h->dalloc<int>(N);
             h->ozeb = h->dalloc<int>(N);
+            encode_digit_planes(&h->oz_tmA, h->ozA, N, h->ozKpad, OZ_TM);
+            encode_digit_planes(&h->oz_tmB, h->ozB, N, h->ozKpad, OZ_TN);
             CK(raise_smem_limit((const void*)k_oz_gemm, oz_smem_bytes()));
             int occ_oz = 0;
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_oz, k_oz_gemm, OZ_THREADS, oz_smem_bytes()));
