@@ -170,13 +170,16 @@ __device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t adesc, uin
         :: "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(IDESC_TF32_128x128), "r"(acc));
 }
 
+// Waits for the phase of an mbarrier, bounded by WAIT_LIMIT_NS.  Each try
+// suspends the thread in hardware for up to ~1 us (woken when the phase
+// completes), so waiting warps do not spin on the issue slots of the working ones.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase) {
     const unsigned long long t0 = global_ns();
     for (;;) {
         uint32_t done;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(mbar), "r"(phase) : "memory");
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(mbar), "r"(phase), "r"(1000u) : "memory");
         if (done) return true;
         if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
     }
@@ -321,7 +324,9 @@ __device__ bool flush_tile_tcgen05(const UpdArgs& a, int k, int i0, int j0, unsi
 // CHARGE = 1: charge-channel field (complex Delta, pair mode); a template
 // parameter so that the spin-channel kernel carries none of its code.
 template <int CHARGE>
-__global__ void __launch_bounds__(UPD_THREADS, 1) k_update_slice(UpdArgs a) {
+// At most 85 registers (three CTAs per SM): several chains' cooperative slice
+// grids must be resident together.
+__global__ void __launch_bounds__(UPD_THREADS, 3) k_update_slice(UpdArgs a) {
     extern __shared__ double upd_smem[];
     const int N = a.N, W = a.W, nd = a.nd;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -459,22 +464,24 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_update_slice(UpdArgs a) {
                             test();
                         }
                     } else {
-                        if (threadIdx.x == 32) {
-                            a.msite[kk] = cursor + tf;
-                            a.mcoef[kk] = c;
-                            a.s[cursor + tf] = (int8_t)(-sw[tf]);
-                        }
-                        // x and y of the move at the later window positions: to the
-                        // recursion of phase C (global) and to the trailing update
-                        for (int p = (int)threadIdx.x - 32; p < rest; p += blockDim.x - 32) {
-                            const int q = tf + 1 + p;
-                            const double xq = c * Gw[q * ld + tf];
-                            xs[q] = xq;
-                            a.xw[kk * W + q] = xq;
-                            a.yw[kk * W + q] = -Gw[tf * ld + q];
-                        }
+                        // x of the move at the later window positions (warp 1), for the
+                        // trailing update
+                        if (warp == 1 && lane < rest) xs[tf + 1 + lane] = c * Gw[(tf + 1 + lane) * ld + tf];
                         asm volatile("bar.sync 1, %0;" :: "r"(UPD_THREADS - 32) : "memory");
-                        if (warp != 4) {
+                        if (warp == 4) {
+                            // the move and its x, y at the later window positions, to
+                            // the recursion of phase C (global stores, off the FP64 warps)
+                            if (lane == 0) {
+                                a.msite[kk] = cursor + tf;
+                                a.mcoef[kk] = c;
+                                a.s[cursor + tf] = (int8_t)(-sw[tf]);
+                            }
+                            if (lane < rest) {
+                                const int q = tf + 1 + lane;
+                                a.xw[kk * W + q] = xs[q];
+                                a.yw[kk * W + q] = -Gw[tf * ld + q];
+                            }
+                        } else {
                             // the off-diagonal trailing block, G(q,p) += x_q G(tf,p) for
                             // q, p > tf (column and row tf are read only), packed 32
                             // entries per warp instruction over warps 1-3 and 5-7 (warp 4
