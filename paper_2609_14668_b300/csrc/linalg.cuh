@@ -156,26 +156,32 @@ __device__ void qr_publish(const QRArgs& q, const double* col, int j, bool copy)
     }
 }
 
-// Householder reflector of column j (rows j..n-1), in place in `col`; whole CTA.
+// Householder reflector of column j (rows j..n-1), in place in `col`; whole CTA
+// (256 threads).  The scalars (norm, beta, tau, 1/(alpha - beta)) are computed
+// by one thread and shared: redundant FP64 square roots and reciprocals in
+// every warp would each hold an FP64 unit.  red: >= 140 doubles.
 __device__ void qr_make_reflector(const QRArgs& q, double* col, int j, double* red) {
     const int n = q.n;
     double s = 0.0;
     for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) { const double x = col[i]; s = fma(x, x, s); }
-    s = block_sum(s, red);
-    const double alpha = col[j];
-    double tau = 0.0, beta = alpha, scale = 0.0;
-    if (s > 0.0) {
-        const double nrm = sqrt(fma(alpha, alpha, s));
-        beta = alpha <= 0.0 ? nrm : -nrm;
-        tau = (beta - alpha) / beta;
-        scale = 1.0 / (alpha - beta);
-    }
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) col[i] *= scale;
+    s = block_sum256(s, red);
     if (threadIdx.x == 0) {
+        const double alpha = col[j];
+        double tau = 0.0, beta = alpha, scale = 0.0;
+        if (s > 0.0) {
+            const double nrm = sqrt(fma(alpha, alpha, s));
+            beta = alpha <= 0.0 ? nrm : -nrm;
+            tau = (beta - alpha) * recip_fast(beta);
+            scale = recip_fast(alpha - beta);
+        }
         col[j] = beta;
         q.tau[j] = tau;
+        red[138] = scale;
         if (!isfinite(beta) || !isfinite(tau)) flag_error(q.st, DERR_NUMERIC, 100);
     }
+    __syncthreads();
+    const double scale = red[138];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) col[i] *= scale;
     __syncthreads();
 }
 
@@ -192,7 +198,7 @@ __device__ __forceinline__ void qr_apply_warp(const double* __restrict__ v, doub
 __device__ void qr_apply_block(const double* __restrict__ v, double tau, double* col, int j, int n, double* red) {
     double w = 0.0;
     for (int i = j + threadIdx.x; i < n; i += blockDim.x) w = fma(v[i - j], col[i], w);
-    w = block_sum(w, red) * tau;
+    w = block_sum256(w, red) * tau;
     for (int i = j + threadIdx.x; i < n; i += blockDim.x) col[i] = fma(-w, v[i - j], col[i]);
     __syncthreads();
 }
@@ -201,7 +207,7 @@ __device__ void qr_apply_block(const double* __restrict__ v, double tau, double*
 // cols_in_smem) ceil(n / gridDim.x) * n doubles holding this CTA's columns.
 __global__ void __launch_bounds__(256) k_qr_cols(QRArgs q, int cols_in_smem) {
     extern __shared__ double qr_smem[];
-    __shared__ double red[33];
+    __shared__ double red[140];
     __shared__ int s_abort;
     const int n = q.n, G = gridDim.x, me = blockIdx.x;
     const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -314,37 +320,43 @@ struct LUArgs {
     DevStatus* st;
 };
 
-// pivot search, swap and scaling of column j (rows j..n-1), whole CTA
+// pivot search, swap and scaling of column j (rows j..n-1), whole CTA (256
+// threads).  Magnitudes are compared as the integer images of |x| (ties to the
+// smaller row, a NaN wins and is flagged), so the search uses no FP64
+// instruction; one thread forms the pivot's reciprocal.
 __device__ void lu_pivot_column(const LUArgs& q, double* col, int j, double* redv, int* redi) {
     const int n = q.n;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    double best = -1.0;
+    long long best = -1;
     int bi = j;
     for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
-        const double v = fabs(col[i]);
-        if (v > best) { best = v; bi = i; }
+        const long long m = __double_as_longlong(col[i]) & 0x7fffffffffffffffll;
+        if (m > best) { best = m; bi = i; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
-    if (lane == 0) { redv[warp] = best; redi[warp] = bi; }
+    long long* redb = reinterpret_cast<long long*>(redv);
+    if (lane == 0) { redb[warp] = best; redi[warp] = bi; }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < nwarp; ++w)
-            if (redv[w] > best || (redv[w] == best && redi[w] < bi)) { best = redv[w]; bi = redi[w]; }
+            if (redb[w] > best || (redb[w] == best && redi[w] < bi)) { best = redb[w]; bi = redi[w]; }
         const double t = col[j];
         col[j] = col[bi];
         col[bi] = t;
-        redv[32] = col[j];
+        const double pv = col[j];
+        redv[32] = pv;
         redi[32] = bi;
         q.piv[j] = bi;
-        if (!(best > 0.0) || !isfinite(best)) flag_error(q.st, DERR_NUMERIC, 110);
+        if (best <= 0 || !finite_bits(pv)) flag_error(q.st, DERR_NUMERIC, 110);
+        redv[33] = recip_fast(pv);
     }
     __syncthreads();
-    const double inv = 1.0 / redv[32];
+    const double inv = redv[33];
     for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) col[i] *= inv;
     __syncthreads();
 }
@@ -376,7 +388,7 @@ __device__ __forceinline__ void lu_apply_warp(const double* __restrict__ l, int 
 
 __global__ void __launch_bounds__(256) k_lu_cols(LUArgs q, int cols_in_smem) {
     extern __shared__ double lu_smem[];
-    __shared__ double redv[33];
+    __shared__ double redv[34];
     __shared__ int redi[33];
     __shared__ int s_abort, s_piv;
     const int n = q.n, G = gridDim.x, me = blockIdx.x;

@@ -89,25 +89,6 @@ __device__ __forceinline__ int win_phys(const UpdArgs& a, int c0, int t) {   // 
     return a.pair ? c0 + (t >> 1) : c0 + t;
 }
 
-// 1 / r from the hardware estimate y0 (relative error below 2^-19.9 on this
-// part, measured) by one cubic step y0 (1 + e + e^2), e = 1 - r y0: the error
-// e^3 < 2^-59 is below FP64 rounding, in three dependent FP64 operations
-__device__ __forceinline__ double recip_fast(double r) {
-    double y0;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(r));
-    const double e = fma(-r, y0, 1.0);
-    return fma(y0, fma(e, e, e), y0);
-}
-
-// |x| > t for t >= 0 (not NaN), on the bit patterns (non-negative doubles order
-// as their integer images): keeps the comparison off the FP64 unit
-__device__ __forceinline__ bool abs_gt(double x, double t) {
-    return (__double_as_longlong(x) & 0x7fffffffffffffffll) > __double_as_longlong(t);
-}
-__device__ __forceinline__ bool finite_bits(double x) {
-    return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
-}
-
 // 1 / r: hardware reciprocal estimate refined by two Newton steps
 __device__ __forceinline__ double recip_nr(double r) {
     double y;
