@@ -65,9 +65,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tau-sweeps", type=int, default=15,
                     help="extra sweeps per chain (after the timed and e2e ones) for the autocorrelation time")
-    ap.add_argument("--precision", type=int, default=3, choices=[0, 1, 2, 3],
+    ap.add_argument("--precision", type=int, default=3, choices=[0, 1, 2, 3, 6, 7],
                     help="bit 0: split-TF32 tensor-core flush (the L=24 precision workload); bit 1: stabilisation "
-                         "products on the BF16 tensor cores with FP64 accuracy (Ozaki); 0: plain FP64")
+                         "products on the BF16 tensor cores with FP64 accuracy (Ozaki); bit 2 (with bit 1): blocked "
+                         "solves of G with those products as couplings; 0: plain FP64")
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 sweep")
     ap.add_argument("--update-ctas", type=int, default=0,
                     help="CTAs of the cooperative slice kernel per chain (0: one per SM)")

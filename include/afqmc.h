@@ -85,8 +85,12 @@ typedef struct {
                               FP32 accumulate) subtracted from the FP64 G.  Bit 1: the matrix
                               products of the stabilisation (stack extension, middle matrix and G
                               recomputation) on the BF16 tensor cores by the Ozaki scheme,
-                              FP64-accurate (8 digits of 7 bits, exact FP32 class sums).  Ratios,
-                              x/y recursion, wraps, QR, LU and measurements stay FP64 */
+                              FP64-accurate (8 digits of 7 bits, exact FP32 class sums).  Bit 2
+                              (needs bit 1): the triangular solves of the G recomputation blocked,
+                              their couplings as bit-1 products and only diagonal blocks of at most
+                              64 in FP64 (less latency for a chain alone; with several chains on one
+                              GPU the many short tensor-core launches cost more than they save).
+                              Ratios, x/y recursion, wraps, QR, LU and measurements stay FP64 */
     int32_t measure;       /* 1: accumulate observables at every recomputation of G in a sweep */
     int32_t chain;         /* chain index: selects the random stream */
     int32_t device;        /* CUDA device ordinal */

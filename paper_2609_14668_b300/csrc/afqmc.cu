@@ -95,6 +95,7 @@ struct afqmc_handle {
            *DbL = nullptr, *DsL = nullptr;
     unsigned int* flags = nullptr;
     int* piv = nullptr;            // LU pivots of the middle matrix of G
+    int* lperm = nullptr;          // precision bit 2: combined LU row order (blocked solves)
     unsigned int epoch = 0;
     double2* blocks = nullptr;     // 4 operators x Nc x 4
     double2 *tw1 = nullptr, *tw2 = nullptr;
@@ -330,13 +331,28 @@ void gemm_oz(afqmc_handle* h, const double* A, int transA, const double* B, int 
             src = h->Wk[4];
         }
         Scope sc(h, AFQMC_K_GEMM);
-        k_oz_split<<<(n * 32 + 255) / 256, 256, 0, h->stream>>>(src, n, n, n, out, Kp, ex);
+        k_oz_split<<<(n * 32 + 255) / 256, 256, 0, h->stream>>>(src, n, n, n, out, n, Kp, Kp, ex);
     };
     split(A, transA != 0, h->ozA, h->ozea);
     split(B, transB == 0, h->ozB, h->ozeb);
     OzArgs g{h->ozA, h->ozB, h->ozea, h->ozeb, n, n, Kp, C, n, alpha, beta, rs, cs, rs_inv, cs_inv, h->st};
     dim3 grid((n + OZ_TN - 1) / OZ_TN, (n + OZ_TM - 1) / OZ_TM);
     Scope sc(h, AFQMC_K_GEMM);
+    k_oz_gemm<<<grid, OZ_THREADS, oz_smem_bytes(), h->stream>>>(h->oz_tmA, h->oz_tmB, g);
+    CK(cudaGetLastError());
+}
+
+// C[i][j] = alpha sum_k A[i][k] B[j][k] + beta C[i][j] for i < m, j < n, k < K, on
+// row segments (leading dimensions lda, ldb, ldc <= N): the Ozaki product of the
+// blocked solves, FP64-accurate, counted in kernel family `cat`.
+void gemm_rows_oz(afqmc_handle* h, const double* A, int lda, int m, const double* B, int ldb, int n, int K,
+                  double* C, int ldc, double alpha, double beta, int cat) {
+    const int Kp = h->ozKpad, Kw = (K + OZ_KC - 1) / OZ_KC * OZ_KC;
+    { Scope sc(h, cat); k_oz_split<<<(m * 32 + 255) / 256, 256, 0, h->stream>>>(A, m, K, lda, h->ozA, h->N, Kp, Kw, h->ozea); }
+    { Scope sc(h, cat); k_oz_split<<<(n * 32 + 255) / 256, 256, 0, h->stream>>>(B, n, K, ldb, h->ozB, h->N, Kp, Kw, h->ozeb); }
+    OzArgs g{h->ozA, h->ozB, h->ozea, h->ozeb, m, n, Kw, C, ldc, alpha, beta, nullptr, nullptr, 0, 0, h->st};
+    dim3 grid((n + OZ_TN - 1) / OZ_TN, (m + OZ_TM - 1) / OZ_TM);
+    Scope sc(h, cat);
     k_oz_gemm<<<grid, OZ_THREADS, oz_smem_bytes(), h->stream>>>(h->oz_tmA, h->oz_tmB, g);
     CK(cudaGetLastError());
 }
@@ -371,15 +387,16 @@ void qr(afqmc_handle* h, double* At) {
     CK(cudaLaunchCooperativeKernel((void*)k_qr_cols, grid, 256, args, smem, h->stream));
 }
 
-// P A = L U of the column-major A (At) in place, pivots in h->piv.
-void lu(afqmc_handle* h, double* At) {
+// P A = L U of the column-major A (At) in place, pivots in h->piv; with Fr also the
+// row-major factor with the swaps applied to L, and the row order in h->lperm.
+void lu(afqmc_handle* h, double* At, double* Fr = nullptr) {
     const int n = h->N;
     h->epoch += 1;
     if (h->epoch == 0) {
         CK(cudaMemsetAsync(h->flags, 0, sizeof(unsigned int) * n, h->stream));
         h->epoch = 1;
     }
-    LUArgs q{At, h->piv, h->flags, h->epoch, n, h->st};
+    LUArgs q{At, h->piv, h->flags, h->epoch, n, h->st, Fr, Fr ? h->lperm : nullptr};
     const int grid = std::min(h->sms, n);
     int in_smem = h->qr_smem_cols ? 1 : 0;
     const size_t smem = sizeof(double) * (size_t)n * (in_smem ? 1 + (n + grid - 1) / grid : 1);
@@ -412,6 +429,60 @@ void launch_backsolve(afqmc_handle* h, const double* Rt, const double* Yt, doubl
     Scope sc(h, AFQMC_K_QRAUX);
     if (col_small(n)) k_backsolve<8, 8><<<cpb_grid(n, n), 256, cpb_smem(n), h->stream>>>(Rt, Yt, Xt, n, n, xs, h->st);
     else k_backsolve<4, 16><<<cpb_grid(n, n), 256, cpb_smem(n), h->stream>>>(Rt, Yt, Xt, n, n, xs, h->st);
+    CK(cudaGetLastError());
+}
+
+// Blocked triangular solves on the rows of Yt (each row one right-hand side),
+// columns r0 .. r1 of the system: with the row-major LU factor Fr, lower (unit
+// L, forward) or upper (U, backward).  The range is halved (in units of 32)
+// down to blocks of at most TRSM_LEAF, which k_trsm_leaf solves in FP64; the
+// coupling between the halves is one Ozaki product per split:
+//   forward:  Y[:, I2] -= Y[:, I1] L[I2, I1]^T   after solving I1,
+//   backward: Y[:, I1] -= Y[:, I2] U[I1, I2]^T   after solving I2,
+// so nearly all of the n^3 flops of a solve with n right-hand sides run on the
+// tensor cores.  Both operands of a product are row segments (rows of Yt and of
+// Fr), as the digit split wants them.
+void trsm_blocked(afqmc_handle* h, const double* Fr, double* Yt, int r0, int r1, bool upper) {
+    const int n = h->N, nb = r1 - r0;
+    if (nb <= TRSM_LEAF) {
+        const int grid = (n + 7) / 8;
+        Scope sc(h, AFQMC_K_QRAUX);
+        if (upper) k_trsm_leaf<1><<<grid, 256, 0, h->stream>>>(Fr, Yt, n, n, r0, nb);
+        else k_trsm_leaf<0><<<grid, 256, 0, h->stream>>>(Fr, Yt, n, n, r0, nb);
+        CK(cudaGetLastError());
+        return;
+    }
+    const int mid = r0 + ((nb + 31) / 32 / 2) * 32;
+    if (!upper) {
+        trsm_blocked(h, Fr, Yt, r0, mid, false);
+        gemm_rows_oz(h, Yt + r0, n, n, Fr + (size_t)mid * n + r0, n, r1 - mid, mid - r0, Yt + mid, n, -1.0, 1.0,
+                     AFQMC_K_QRAUX);
+        trsm_blocked(h, Fr, Yt, mid, r1, false);
+    } else {
+        trsm_blocked(h, Fr, Yt, mid, r1, true);
+        gemm_rows_oz(h, Yt + mid, n, n, Fr + (size_t)r0 * n + mid, n, mid - r0, r1 - mid, Yt + r0, n, -1.0, 1.0,
+                     AFQMC_K_QRAUX);
+        trsm_blocked(h, Fr, Yt, r0, mid, true);
+    }
+}
+
+// X = Db_L^-1 M^-1 rhs (rows of Xt), with P M = L U from lu(h, Mt, Fr) and the
+// right-hand sides the columns of (rows of `in` scaled by rs): P (rs .* in) is
+// gathered and transposed into Yt, solved in place by the blocked solves, and
+// divided by Db_L into Xt.
+void solve_blocked(afqmc_handle* h, const double* Fr, const double* in, const double* rs, int rs_inv, double* Yt,
+                   double* Xt) {
+    const int n = h->N;
+    {
+        dim3 b(32, 8), g((n + 31) / 32, (n + 31) / 32);
+        Scope sc(h, AFQMC_K_QRAUX);
+        k_transpose_perm<<<g, b, 0, h->stream>>>(in, Yt, n, h->lperm, rs, rs_inv);
+    }
+    CK(cudaGetLastError());
+    trsm_blocked(h, Fr, Yt, 0, n, false);
+    trsm_blocked(h, Fr, Yt, 0, n, true);
+    const size_t nn = (size_t)n * n;
+    { Scope sc(h, AFQMC_K_QRAUX); k_div_cols_check<<<(unsigned)std::min<size_t>((nn + 255) / 256, 4u * h->sms), 256, 0, h->stream>>>(Yt, Xt, n, h->DbL, h->st); }
     CK(cudaGetLastError());
 }
 
@@ -472,16 +543,24 @@ void form_green(afqmc_handle* h, const UDTe& R, const UDTe& Lt, double* Gout, do
     double* Mt = h->Wk[0];   // M column-major = M^T row-major
     gemm(h, Lt.Ut, 0, R.Ut, 1, Mt, 1.0, 0.0, h->DbL, 1, h->DbR, 1);
     gemm(h, Lt.T, 0, R.T, 1, Mt, 1.0, 1.0, h->DsL, 0, h->DsR, 0);
-    lu(h, Mt);
+    // precision bit 2: blocked solves with their couplings on the tensor cores,
+    // from the row-major factor Fr; otherwise the column-step FP64 solves
+    const bool blocked = (h->p.precision & 4) != 0;
+    double* Fr = blocked ? h->Wk[3] : nullptr;
+    lu(h, Mt, Fr);
     double* Yt = h->Wk[1];   // Y = Db_R^-1 U_R^T, column-major
-    {
-        dim3 b(32, 8), g((n + 31) / 32, (n + 31) / 32);
-        Scope sc(h, AFQMC_K_QRAUX);
-        k_transpose_scale<<<g, b, 0, h->stream>>>(R.Ut, Yt, n, n, h->DbR, 1, nullptr, 0);
-    }
-    launch_fwdsolve(h, Mt, h->piv, Yt, n);
     double* Wt = h->Wk[2];
-    launch_backsolve(h, Mt, Yt, Wt, n, h->DbL);
+    if (blocked) {
+        solve_blocked(h, Fr, R.Ut, h->DbR, 1, Yt, Wt);
+    } else {
+        {
+            dim3 b(32, 8), g((n + 31) / 32, (n + 31) / 32);
+            Scope sc(h, AFQMC_K_QRAUX);
+            k_transpose_scale<<<g, b, 0, h->stream>>>(R.Ut, Yt, n, n, h->DbR, 1, nullptr, 0);
+        }
+        launch_fwdsolve(h, Mt, h->piv, Yt, n);
+        launch_backsolve(h, Mt, Yt, Wt, n, h->DbL);
+    }
     gemm(h, Lt.Ut, 1, Wt, 1, Gout, 1.0, 0.0, nullptr, 0, nullptr, 0);
     const size_t nn = (size_t)n * n;
     if (G0t) {
@@ -491,13 +570,17 @@ void form_green(afqmc_handle* h, const UDTe& R, const UDTe& Lt, double* Gout, do
         gemm(h, Lt.T, 1, Yt, 1, G0t, -1.0, 0.0, nullptr, 0, nullptr, 0);
     }
     if (Gt0) {
-        {
-            dim3 b(32, 8), g((n + 31) / 32, (n + 31) / 32);
-            Scope sc(h, AFQMC_K_QRAUX);
-            k_transpose_scale<<<g, b, 0, h->stream>>>(R.T, Yt, n, n, h->DsR, 0, nullptr, 0);
+        if (blocked) {
+            solve_blocked(h, Fr, R.T, h->DsR, 0, Yt, Wt);
+        } else {
+            {
+                dim3 b(32, 8), g((n + 31) / 32, (n + 31) / 32);
+                Scope sc(h, AFQMC_K_QRAUX);
+                k_transpose_scale<<<g, b, 0, h->stream>>>(R.T, Yt, n, n, h->DsR, 0, nullptr, 0);
+            }
+            launch_fwdsolve(h, Mt, h->piv, Yt, n);
+            launch_backsolve(h, Mt, Yt, Wt, n, h->DbL);
         }
-        launch_fwdsolve(h, Mt, h->piv, Yt, n);
-        launch_backsolve(h, Mt, Yt, Wt, n, h->DbL);
         gemm(h, Lt.Ut, 1, Wt, 1, Gt0, 1.0, 0.0, nullptr, 0, nullptr, 0);
     }
 }
@@ -829,8 +912,9 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         return bad("twist angles theta1, theta2 must be in [0, 1)");
     if (P.hs_channel != 0 && P.hs_channel != 1)
         return bad("hs_channel must be 0 (spin channel, Eq. SzHS) or 1 (charge channel, Eq. DensityHS)");
-    if (P.precision < 0 || P.precision > 3)
-        return bad("precision must be 0..3 (bit 0: split-TF32 flush, bit 1: tensor-core FP64-accurate stabilisation products)");
+    if (P.precision < 0 || P.precision > 7 || ((P.precision & 4) && !(P.precision & 2)))
+        return bad("precision must be 0..7 (bit 0: split-TF32 flush, bit 1: tensor-core FP64-accurate stabilisation "
+                   "products, bit 2: blocked solves of G on them, needs bit 1)");
     const double Mr = P.beta / P.dtau;
     const int M = (int)std::llround(Mr);
     if (M < 1 || std::fabs(M * P.dtau - P.beta) > 1e-9) return bad("beta must be an integer multiple of dtau");
@@ -974,6 +1058,7 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
             h->ozB = h->dalloc<__nv_bfloat16>((size_t)OZ_S * N * h->ozKpad);
             h->ozea = h->dalloc<int>(N);
             h->ozeb = h->dalloc<int>(N);
+            if (P.precision & 4) h->lperm = h->dalloc<int>(N);
             encode_digit_planes(&h->oz_tmA, h->ozA, N, h->ozKpad, OZ_TM);
             encode_digit_planes(&h->oz_tmB, h->ozB, N, h->ozKpad, OZ_TN);
             CK(raise_smem_limit((const void*)k_oz_gemm, oz_smem_bytes()));

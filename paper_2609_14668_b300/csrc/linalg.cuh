@@ -110,6 +110,99 @@ __global__ void k_transpose_scale(const double* __restrict__ in, double* __restr
     }
 }
 
+// out[j][i] = in[perm[i]][j] * rs[perm[i]] (or / rs[perm[i]] with rs_inv), n x n
+// row-major: the transpose of the row-permuted, row-scaled input (the right-hand
+// sides P Y of the blocked solves, one per row of out).  perm must be a
+// permutation of [0, n).
+__global__ void k_transpose_perm(const double* __restrict__ in, double* __restrict__ out, int n,
+                                 const int* __restrict__ perm, const double* rs, int rs_inv) {
+    __shared__ double tile[32][33];
+    const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int i = bi + y, j = bj + threadIdx.x;
+        double v = 0.0;
+        if (i < n && j < n) {
+            const int r = perm[i];
+            v = in[(size_t)r * n + j];
+            if (rs) v = rs_inv ? v / rs[r] : v * rs[r];
+        }
+        tile[y][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int j = bj + y, i = bi + threadIdx.x;
+        if (i < n && j < n) out[(size_t)j * n + i] = tile[threadIdx.x][y];
+    }
+}
+
+// Diagonal-block step of the blocked triangular solves.  Every row c of Yt (a
+// right-hand side; one warp each) has its entries r0 .. r0+nb replaced by
+// L_bb^-1 y (UPPER = 0: the unit lower triangle) or U_bb^-1 y (UPPER = 1: the
+// upper triangle with its diagonal) of the block at (r0, r0) of the row-major LU
+// factor Fr.  nb <= TRSM_LEAF: lane l holds entries l and l + 32.  The block
+// is staged transposed in shared memory (Ls[j][i] = the coefficient of row i in
+// step j) with zeros where a step must leave a row alone, so a step is one FMA
+// instruction per group of 32 rows it can reach: the FP64 unit of this part
+// takes a warp instruction per ~64 cycles however many lanes are busy.
+constexpr int TRSM_LEAF = 64;
+template <int UPPER>
+__global__ void __launch_bounds__(256) k_trsm_leaf(const double* __restrict__ Fr, double* Yt, int n, int nrhs,
+                                                   int r0, int nb) {
+    __shared__ double Ls[TRSM_LEAF][TRSM_LEAF + 1];
+    __shared__ double dinv[TRSM_LEAF];
+    for (int idx = threadIdx.x; idx < TRSM_LEAF * TRSM_LEAF; idx += blockDim.x) {
+        const int i = idx / TRSM_LEAF, j = idx % TRSM_LEAF;
+        double v = 0.0;
+        if (i < nb && j < nb && (UPPER ? i < j : i > j)) v = Fr[(size_t)(r0 + i) * n + r0 + j];
+        Ls[j][i] = v;
+    }
+    if (UPPER)
+        for (int j = threadIdx.x; j < nb; j += blockDim.x) dinv[j] = 1.0 / Fr[(size_t)(r0 + j) * n + r0 + j];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int c = blockIdx.x * nw + warp; c < nrhs; c += gridDim.x * nw) {
+        double* y = Yt + (size_t)c * n + r0;
+        double y0 = lane < nb ? y[lane] : 0.0;
+        double y1 = lane + 32 < nb ? y[lane + 32] : 0.0;
+        if (!UPPER) {
+            // step j: y_i -= L_ij y_j for i > j
+            for (int j = 0; j < nb - 1; ++j) {
+                const double yj = __shfl_sync(0xffffffffu, j < 32 ? y0 : y1, j & 31);
+                if (j < 31) y0 = fma(-Ls[j][lane], yj, y0);
+                if (nb > 32) y1 = fma(-Ls[j][lane + 32], yj, y1);
+            }
+        } else {
+            // step j (descending): x_j = y_j / U_jj, then y_i -= U_ij x_j for i < j
+            for (int j = nb - 1; j >= 0; --j) {
+                const double xj = __shfl_sync(0xffffffffu, j < 32 ? y0 : y1, j & 31) * dinv[j];
+                if (lane == (j & 31)) {
+                    if (j < 32) y0 = xj;
+                    else y1 = xj;
+                }
+                if (j >= 1) y0 = fma(-Ls[j][lane], xj, y0);
+                if (j >= 33) y1 = fma(-Ls[j][lane + 32], xj, y1);
+            }
+        }
+        if (lane < nb) y[lane] = y0;
+        if (lane + 32 < nb) y[lane + 32] = y1;
+    }
+}
+
+// out[c][i] = in[c][i] / xs[i] (xs may be null: a copy), n x n; flags
+// DERR_NUMERIC on a non-finite result (the end of the solves of G).
+__global__ void k_div_cols_check(const double* __restrict__ in, double* out, int n, const double* __restrict__ xs,
+                                 DevStatus* st) {
+    bool bad = false;
+    const size_t nn = (size_t)n * n;
+    for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < nn; o += (size_t)gridDim.x * blockDim.x) {
+        double v = in[o];
+        if (xs) v /= xs[o % n];
+        if (!isfinite(v)) bad = true;
+        out[o] = v;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) flag_error(st, DERR_NUMERIC, 102);
+}
+
 // ---------------------------------------------------------------------------
 // Householder QR of a column-major n x n matrix A (array At, row c = column c).
 // On exit: R in the upper triangle (At[c][i], i <= c), reflector j stored below
@@ -314,10 +407,19 @@ __device__ __forceinline__ void store_vec(double* dst, int lo, int hi, const dou
 // column storage and flag protocol as k_qr_cols; the critical path of a step
 // holds one reduction (the pivot search) instead of the two of a Householder
 // step.
+// In At the multipliers of column j stay in the row order of step j (the
+// column-step solves replay the swaps in turn).  With Fr set, the kernel also
+// writes the factor row-major with every later swap applied to the earlier
+// multipliers (P A = L U with P = P_{n-2} ... P_0 and the final L, as the
+// blocked solves need it), and lperm (the combined row order: row i of P A is
+// row lperm[i] of A): the owner of a finished column swaps its two entries in
+// Fr at every later step, CTA 0 keeps lperm.  Neither is read during the
+// factorisation.
 // ---------------------------------------------------------------------------
 struct LUArgs {
     double* At; int* piv; unsigned int* flags; unsigned int epoch; int n;
     DevStatus* st;
+    double* Fr; int* lperm;     // optional (both or neither)
 };
 
 // pivot search, swap and scaling of column j (rows j..n-1), whole CTA (256
@@ -370,6 +472,9 @@ __device__ void lu_publish(const LUArgs& q, const double* col, int j, bool copy)
         __threadfence();
         atomicExch(&q.flags[j], q.epoch);
     }
+    // the row-major copy is read only after the kernel: written after the flag
+    if (q.Fr)
+        for (int i = threadIdx.x; i < q.n; i += blockDim.x) q.Fr[(size_t)i * q.n + j] = col[i];
 }
 
 // apply step j (swap rows j, p; a_i -= l_ij a_j for i > j) to a column; one warp
@@ -404,6 +509,8 @@ __global__ void __launch_bounds__(256) k_lu_cols(LUArgs q, int cols_in_smem) {
             double* d = col(c);
             for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = q.At[(size_t)c * n + i];
         }
+    if (me == 0 && q.lperm)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) q.lperm[i] = i;
     __syncthreads();
     if (me == 0) {
         lu_pivot_column(q, col(0), 0, redv, redi);
@@ -423,6 +530,21 @@ __global__ void __launch_bounds__(256) k_lu_cols(LUArgs q, int cols_in_smem) {
         __syncthreads();
         if (s_abort) return;
         const int p = s_piv;
+        if (q.Fr && p != j) {
+            // step j's swap on the multipliers of this CTA's finished columns (c < j; warp 0,
+            // whose memory latency the other warps' FP64 work covers), and on the row order
+            for (int c = me + threadIdx.x * G; threadIdx.x < 32 && c < j; c += 32 * G) {
+                double* f = q.Fr + c;
+                const double a = f[(size_t)j * n], b = f[(size_t)p * n];
+                f[(size_t)j * n] = b;
+                f[(size_t)p * n] = a;
+            }
+            if (me == 0 && threadIdx.x == 32) {
+                const int a = q.lperm[j], b = q.lperm[p];
+                q.lperm[j] = b;
+                q.lperm[p] = a;
+            }
+        }
         const double* colj = q.At + (size_t)j * n;
         stage_column(colj, l, j + 1, n, 0);
         __syncthreads();

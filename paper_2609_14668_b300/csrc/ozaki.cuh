@@ -70,10 +70,11 @@ __device__ __forceinline__ double pow2i(int e) {
 inline size_t oz_smem_bytes() { return 2 * OZ_STAGE + 1024; }   // two stages (+ alignment slack)
 
 // rows of X (rows x K, row-major, leading dimension ld) into OZ_S digit planes
-// out[s][row][0..Kpad) (BF16, zero beyond K) and the row exponents ex[row];
-// one warp per row.
-__global__ void k_oz_split(const double* __restrict__ X, int rows, int K, int ld, __nv_bfloat16* out, int Kpad,
-                           int* ex) {
+// out[s][row][0..Kw) (BF16, zero for K <= k < Kw) and the row exponents ex[row];
+// one warp per row.  The planes are prows x Kpad (prows >= rows, Kpad >= Kw), the
+// shape of the tensor map that stages them.
+__global__ void k_oz_split(const double* __restrict__ X, int rows, int K, int ld, __nv_bfloat16* out, int prows,
+                           int Kpad, int Kw, int* ex) {
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= rows) return;
@@ -85,9 +86,9 @@ __global__ void k_oz_split(const double* __restrict__ X, int rows, int K, int ld
     int e = 0;
     if (mx > 0.0) frexp(mx, &e);          // mx = f 2^e, f in [0.5, 1): |x| 2^-e < 1
     if (lane == 0) ex[row] = e;
-    const size_t plane = (size_t)rows * Kpad;
+    const size_t plane = (size_t)prows * Kpad;
     constexpr int TOP = OZ_BITS * OZ_S;      // 56 fraction bits kept
-    for (int k = lane; k < Kpad; k += 32) {
+    for (int k = lane; k < Kw; k += 32) {
         // q = a 2^56 rounded to an integer (|q| < 2^56: exact in int64), then balanced
         // base-2^7 digits by integer shifts: d = round(q / 2^shift), q -= d 2^shift
         long long q = k < K ? __double2ll_rn(ldexp(at(k), TOP - e)) : 0ll;

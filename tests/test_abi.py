@@ -36,7 +36,7 @@ def test_binding_names_match_header():
 @pytest.mark.parametrize("field,value,msg", [
     ("L1", 0, "L1"), ("beta", -1.0, "beta"), ("dtau", 0.0, "dtau"), ("n_stab", 7, "n_stab"),
     ("n_delay", 0, "n_delay"), ("theta1", 1.5, "twist"), ("theta2", -0.25, "twist"), ("hs_channel", 2, "charge channel"), ("hs_channel", -1, "hs_channel"),
-    ("precision", 4, "precision"), ("U", -1.0, "U"),
+    ("precision", 4, "precision"), ("precision", 5, "precision"), ("precision", 8, "precision"), ("U", -1.0, "U"),
 ])
 def test_invalid_parameters_rejected_on_host(field, value, msg):
     import paper_2609_14668_b300 as pkg

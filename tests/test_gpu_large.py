@@ -65,7 +65,9 @@ def oracle_case(L, theta, hs, n_delay):
 @pytest.mark.parametrize("L,theta,hs,n_delay,precision", [
     (42, (0.0, 0.0), 0, 64, 0),
     (42, (0.0, 0.0), 0, 64, 2),
+    (42, (0.0, 0.0), 0, 64, 6),
     (24, (0.25, 0.5), 0, 32, 0),
+    (24, (0.25, 0.5), 0, 32, 6),
     (24, (0.0, 0.0), 1, 32, 2),
 ])
 def test_large_matrix_parity(pkg, L, theta, hs, n_delay, precision):

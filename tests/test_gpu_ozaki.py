@@ -1,7 +1,11 @@
 """Stabilisation products on the BF16 tensor cores with FP64 accuracy (Ozaki
-scheme, precision bit 1).  Held to the FP64 parity bar: G recomputed from the
+scheme, precision bit 1), and the blocked solves of G whose couplings are such
+products (precision bit 2).  Held to the FP64 parity bar: G recomputed from the
 stacks matches the oracle to 1e-10 relative, a sweep takes the oracle's
-decisions, with and without a twist and at the full L = 24 size."""
+decisions, with and without a twist and at the full L = 24 size.  The blocked
+solves halve the system in units of 32 down to diagonal blocks of at most 64:
+N = 18 and 36 are one block, N = 72 two blocks and one coupling, N = 144 and
+the ragged N = 162 two levels, N = 1152 five."""
 import numpy as np
 import pytest
 
@@ -26,7 +30,10 @@ def rel_err(a, b):
 
 
 @pytest.mark.parametrize("L,beta,ns,theta,precision", [(3, 3.0, 10, (0.0, 0.0), 2), (6, 6.0, 10, (0.0, 0.0), 2),
-                                                       (6, 6.0, 10, (0.0, 0.0), 3), (3, 3.0, 10, (0.25, 0.5), 2)])
+                                                       (6, 6.0, 10, (0.0, 0.0), 3), (3, 3.0, 10, (0.25, 0.5), 2),
+                                                       (3, 3.0, 10, (0.0, 0.0), 6), (6, 6.0, 10, (0.0, 0.0), 6),
+                                                       (9, 2.0, 10, (0.0, 0.0), 7), (3, 3.0, 10, (0.25, 0.5), 6),
+                                                       (6, 2.0, 10, (0.25, 0.5), 6)])
 def test_green_parity(pkg, L, beta, ns, theta, precision):
     from oracle.dqmc import Model
     m = Model(L, U=3.73, beta=beta, dtau=0.1, theta=theta)
@@ -39,13 +46,14 @@ def test_green_parity(pkg, L, beta, ns, theta, precision):
     ch.close()
 
 
-def test_sweep_lockstep(pkg):
+@pytest.mark.parametrize("precision", [2, 6])
+def test_sweep_lockstep(pkg, precision):
     from oracle.dqmc import Model, Chain
     w = WORKLOADS["L6_beta6"]
     m = Model(w["L"], U=w["U"], beta=w["beta"], dtau=w["dtau"])
     oc = Chain(m, n_delay=w["n_delay"], n_stab=w["n_stab"], seed=2024)
     ch = pkg.Chain(pkg.make_params(L=w["L"], beta=w["beta"], dtau=w["dtau"], U=w["U"], n_delay=w["n_delay"],
-                                   n_stab=w["n_stab"], seed=2024, precision=2))
+                                   n_stab=w["n_stab"], seed=2024, precision=precision))
     st = ch.sweep(1)
     oc.sweep()
     assert st.accepted == oc.accepted
@@ -55,13 +63,26 @@ def test_sweep_lockstep(pkg):
     ch.close()
 
 
-def test_full_size_green(pkg):
-    from oracle.dqmc import Model
-    w = WORKLOADS["L24_beta24"]
-    m = Model(w["L"], U=w["U"], beta=w["beta"], dtau=w["dtau"])
-    f = random_field(m.M, m.N, 424)
+_FULL = {}
+
+
+def full_size_reference():
+    """Field and oracle G(0) at L = 24 (cached: one dense N = 1152 recomputation)."""
+    if not _FULL:
+        from oracle.dqmc import Model
+        w = WORKLOADS["L24_beta24"]
+        m = Model(w["L"], U=w["U"], beta=w["beta"], dtau=w["dtau"])
+        f = random_field(m.M, m.N, 424)
+        _FULL.update(w=w, f=f, G0=m.green_stable(f, 0, w["n_stab"]))
+    return _FULL
+
+
+@pytest.mark.parametrize("precision", [3, 7])
+def test_full_size_green(pkg, precision):
+    ref = full_size_reference()
+    w = ref["w"]
     ch = pkg.Chain(pkg.make_params(L=w["L"], beta=w["beta"], dtau=w["dtau"], U=w["U"], n_delay=w["n_delay"],
-                                   n_stab=w["n_stab"], seed=5, precision=3))
-    ch.set_field(f)
-    assert rel_err(ch.green(0), m.green_stable(f, 0, w["n_stab"])) < TOL
+                                   n_stab=w["n_stab"], seed=5, precision=precision))
+    ch.set_field(ref["f"])
+    assert rel_err(ch.green(0), ref["G0"]) < TOL
     ch.close()

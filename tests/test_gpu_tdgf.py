@@ -25,13 +25,17 @@ def pkg():
     return p
 
 
-@pytest.mark.parametrize("L,beta,ns,theta", [(2, 1.2, 3, (0.0, 0.0)), (3, 1.0, 5, (0.25, 0.5)),
-                                             (6, 0.8, 4, (0.0, 0.0))])
-def test_single_field_matches_oracle(pkg, L, beta, ns, theta):
+@pytest.mark.parametrize("L,beta,ns,theta,precision", [(2, 1.2, 3, (0.0, 0.0), 0), (3, 1.0, 5, (0.25, 0.5), 0),
+                                                       (6, 0.8, 4, (0.0, 0.0), 0), (3, 1.0, 5, (0.25, 0.5), 6),
+                                                       (6, 0.8, 4, (0.0, 0.0), 6)])
+def test_single_field_matches_oracle(pkg, L, beta, ns, theta, precision):
+    """Precision 6: G(tau, 0) through the blocked solves as well (a second set of
+    right-hand sides on the same LU)."""
     from oracle.dqmc import Model
     m = Model(L, U=3.73, beta=beta, dtau=0.1, theta=theta)
     f = random_field(m.M, m.N, 17 + L)
-    ch = pkg.Chain(pkg.make_params(L=L, beta=beta, dtau=0.1, U=3.73, n_delay=4, n_stab=ns, seed=3, theta=theta))
+    ch = pkg.Chain(pkg.make_params(L=L, beta=beta, dtau=0.1, U=3.73, n_delay=4, n_stab=ns, seed=3, theta=theta,
+                                   precision=precision))
     ch.set_field(f)
     pkg.afqmc_measure_td(ch.h)
     C, dDdU, chiF, n = pkg.afqmc_get_td(ch.h)
