@@ -93,10 +93,9 @@ struct afqmc_handle {
     int *msite = nullptr, *ctl = nullptr, *perm = nullptr;
     double *vtmp = nullptr, *Dp = nullptr, *sgn = nullptr, *tau = nullptr, *DbR = nullptr, *DsR = nullptr,
            *DbL = nullptr, *DsL = nullptr;
-    unsigned int* flags = nullptr;
+    double* pubx = nullptr;        // scalar of each column hand-off of the QR and LU kernels
     int* piv = nullptr;            // LU pivots of the middle matrix of G
     int* lperm = nullptr;          // precision bit 2: combined LU row order (blocked solves)
-    unsigned int epoch = 0;
     double2* blocks = nullptr;     // 4 operators x Nc x 4
     double2 *tw1 = nullptr, *tw2 = nullptr;
     DevStatus* st = nullptr;
@@ -371,14 +370,22 @@ void gemm(afqmc_handle* h, const double* A, int transA, const double* B, int tra
     CK(cudaGetLastError());
 }
 
+// the publication buffers of the QR and LU column hand-off (Wk[2] is free
+// during both factorisations), filled with the empty pattern
+double* pub_clear(afqmc_handle* h) {
+    const size_t nn = (size_t)h->N * h->N;
+    double* pub = h->Wk[2];
+    Scope sc(h, AFQMC_K_MISC);
+    k_pub_clear<<<(unsigned)std::min<size_t>((nn + 255) / 256, 4u * h->sms), 256, 0, h->stream>>>(pub, nn, h->pubx,
+                                                                                                  h->N);
+    CK(cudaGetLastError());
+    return pub;
+}
+
 void qr(afqmc_handle* h, double* At) {
     const int n = h->N;
-    h->epoch += 1;
-    if (h->epoch == 0) {   // wrapped: clear the flags once
-        CK(cudaMemsetAsync(h->flags, 0, sizeof(unsigned int) * n, h->stream));
-        h->epoch = 1;
-    }
-    QRArgs q{At, h->tau, h->flags, h->epoch, n, h->st};
+    double* pub = pub_clear(h);
+    QRArgs q{At, h->tau, pub, h->pubx, n, h->st};
     const int grid = std::min(h->sms, n);
     int in_smem = h->qr_smem_cols ? 1 : 0;
     const size_t smem = sizeof(double) * (size_t)n * (in_smem ? 1 + (n + grid - 1) / grid : 1);
@@ -391,12 +398,8 @@ void qr(afqmc_handle* h, double* At) {
 // row-major factor with the swaps applied to L, and the row order in h->lperm.
 void lu(afqmc_handle* h, double* At, double* Fr = nullptr) {
     const int n = h->N;
-    h->epoch += 1;
-    if (h->epoch == 0) {
-        CK(cudaMemsetAsync(h->flags, 0, sizeof(unsigned int) * n, h->stream));
-        h->epoch = 1;
-    }
-    LUArgs q{At, h->piv, h->flags, h->epoch, n, h->st, Fr, Fr ? h->lperm : nullptr};
+    double* pub = pub_clear(h);
+    LUArgs q{At, h->piv, pub, h->pubx, n, h->st, Fr, Fr ? h->lperm : nullptr};
     const int grid = std::min(h->sms, n);
     int in_smem = h->qr_smem_cols ? 1 : 0;
     const size_t smem = sizeof(double) * (size_t)n * (in_smem ? 1 + (n + grid - 1) / grid : 1);
@@ -1068,9 +1071,8 @@ afqmc_status afqmc_create(const afqmc_params* p, void* cuda_stream, afqmc_handle
         }
         h->DbR = h->dalloc<double>(N); h->DsR = h->dalloc<double>(N);
         h->DbL = h->dalloc<double>(N); h->DsL = h->dalloc<double>(N);
-        h->flags = h->dalloc<unsigned int>(N);
+        h->pubx = h->dalloc<double>(N);
         h->piv = h->dalloc<int>(N);
-        CK(cudaMemset(h->flags, 0, sizeof(unsigned int) * N));
         h->st = h->dalloc<DevStatus>(1);
         CK(cudaMemset(h->st, 0, sizeof(DevStatus)));
         h->n_acc = h->dalloc<unsigned long long>(1);

@@ -204,55 +204,104 @@ __global__ void k_div_cols_check(const double* __restrict__ in, double* out, int
 }
 
 // ---------------------------------------------------------------------------
+// Column hand-off of the QR and LU kernels.  Step j of either factorisation
+// needs column j as its owner finished it (the reflector, or the multipliers)
+// and one scalar (tau_j, or the pivot row).  The owner stores them into
+// publication buffers (column j at pub + j n, the scalar at pubx[j]) that were
+// filled with the PUB_EMPTY pattern before the launch.  Every element is
+// stored exactly once and 8-byte stores are single-copy atomic, so a reader
+// knows an element is final as soon as it differs from the pattern: no flag,
+// no memory fence, and readers stage the column while the owner is still
+// writing it.  The scalar is stored first; while a CTA waits, only its thread
+// 0 polls (the scalar), then every thread loads its elements once and polls
+// again only those still empty.  The pattern is a signalling NaN (arithmetic
+// never produces one).  Every wait is bounded by the wait limit.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long PUB_EMPTY = 0x7FF4A5A55A5AA5A5ull;
+
+__device__ __forceinline__ unsigned long long ld_relaxed_b64(const double* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_b64(double* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_f64(double* p, double x) {
+    st_relaxed_b64(p, (unsigned long long)__double_as_longlong(x));
+}
+
+// pub[0..len) and pubx[0..n) <- PUB_EMPTY (before every QR or LU launch).
+__global__ void k_pub_clear(double* pub, size_t len, double* pubx, int n) {
+    const double e = __longlong_as_double((long long)PUB_EMPTY);
+    for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < len; o += (size_t)gridDim.x * blockDim.x)
+        pub[o] = e;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) pubx[i] = e;
+}
+
+// Wait until *p is published (its bits in v).  False on another CTA's failure,
+// or on a timeout, which is flagged with site code `where`.
+__device__ bool await_published(const double* p, unsigned long long& v, DevStatus* st, unsigned long long lim,
+                                int where) {
+    v = ld_relaxed_b64(p);
+    if (v != PUB_EMPTY) return true;
+    const unsigned long long t0 = global_ns();
+    unsigned int ns = 8;
+    for (;;) {
+        __nanosleep(ns);
+        v = ld_relaxed_b64(p);
+        if (v != PUB_EMPTY) return true;
+        if (*(volatile int*)&st->err) return false;
+        if (global_ns() - t0 > lim) {
+            flag_error(st, DERR_TIMEOUT, where);
+            return false;
+        }
+        if (ns < 64) ns <<= 1;
+    }
+}
+
+// dst[i - off] = src[i] for i in [lo, n) from a publication buffer (whole CTA),
+// up to 8 loads per thread in flight.  False as await_published.
+__device__ bool stage_published(const double* src, double* dst, int lo, int n, int off, DevStatus* st,
+                                unsigned long long lim, int where) {
+    constexpr int SB = 8;
+    for (int i0 = lo + threadIdx.x; i0 < n; i0 += SB * blockDim.x) {
+        unsigned long long v[SB];
+#pragma unroll
+        for (int q = 0; q < SB; ++q) {
+            const int i = i0 + q * blockDim.x;
+            v[q] = i < n ? ld_relaxed_b64(src + i) : 0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < SB; ++q) {
+            const int i = i0 + q * blockDim.x;
+            if (i < n) {
+                if (v[q] == PUB_EMPTY && !await_published(src + i, v[q], st, lim, where)) return false;
+                dst[i - off] = __longlong_as_double((long long)v[q]);
+            }
+        }
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // Householder QR of a column-major n x n matrix A (array At, row c = column c).
 // On exit: R in the upper triangle (At[c][i], i <= c), reflector j stored below
 // the diagonal (At[j][i], i > j, implicit 1 at i = j), tau[j].
 // H_j = I - tau_j v_j v_j^T,  A = H_0 H_1 ... H_{n-2} R.
-// Cooperative launch; column c is owned by CTA c % gridDim.x.  flags[j] is set
-// to `epoch` once reflector j is final.
+// Cooperative launch; column c is owned by CTA c % gridDim.x; reflector j and
+// tau_j are handed on through the publication buffers (pub: n x n, pubx: n).
 // ---------------------------------------------------------------------------
 struct QRArgs {
-    double* At; double* tau; unsigned int* flags; unsigned int epoch; int n;
+    double* At; double* tau; double* pub; double* pubx; int n;
     DevStatus* st;
 };
 
-// dst[i - off] = src[i] for i in [lo, n) (whole CTA), through L2, with up to 8
-// loads per thread in flight before their stores: the copy of the published
-// column sits on the critical path of every column step.
-__device__ __forceinline__ void stage_column(const double* __restrict__ src, double* dst, int lo, int n, int off) {
-    constexpr int SB = 8;
-    for (int i0 = lo + threadIdx.x; i0 < n; i0 += SB * blockDim.x) {
-        double v[SB];
-#pragma unroll
-        for (int q = 0; q < SB; ++q) {
-            const int i = i0 + q * blockDim.x;
-            v[q] = i < n ? __ldcg(src + i) : 0.0;
-        }
-#pragma unroll
-        for (int q = 0; q < SB; ++q) {
-            const int i = i0 + q * blockDim.x;
-            if (i < n) dst[i - off] = v[q];
-        }
-    }
-}
-
-// Publish column j (final: R entries above the diagonal, beta on it, the
-// reflector below) to global memory and raise flags[j].
-__device__ void qr_publish(const QRArgs& q, const double* col, int j, bool copy) {
-    double* g = q.At + (size_t)j * q.n;
-    if (copy)
-        for (int i = threadIdx.x; i < q.n; i += blockDim.x) g[i] = col[i];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicExch(&q.flags[j], q.epoch);
-    }
-}
-
-// Householder reflector of column j (rows j..n-1), in place in `col`; whole CTA
-// (256 threads).  The scalars (norm, beta, tau, 1/(alpha - beta)) are computed
-// by one thread and shared: redundant FP64 square roots and reciprocals in
-// every warp would each hold an FP64 unit.  red: >= 140 doubles.
+// Householder reflector of column j (rows j..n-1), in place in `col`, and its
+// publication (tau_j first, then v_j); whole CTA (256 threads).  The scalars
+// (norm, beta, tau, 1/(alpha - beta)) are computed by one thread and shared:
+// redundant FP64 square roots and reciprocals in every warp would each hold an
+// FP64 unit.  red: >= 140 doubles.
 __device__ void qr_make_reflector(const QRArgs& q, double* col, int j, double* red) {
     const int n = q.n;
     double s = 0.0;
@@ -269,12 +318,18 @@ __device__ void qr_make_reflector(const QRArgs& q, double* col, int j, double* r
         }
         col[j] = beta;
         q.tau[j] = tau;
+        st_relaxed_f64(q.pubx + j, tau);
         red[138] = scale;
         if (!isfinite(beta) || !isfinite(tau)) flag_error(q.st, DERR_NUMERIC, 100);
     }
     __syncthreads();
     const double scale = red[138];
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) col[i] *= scale;
+    double* pj = q.pub + (size_t)j * n;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+        const double x = col[i] * scale;
+        col[i] = x;
+        st_relaxed_f64(pj + i, x);
+    }
     __syncthreads();
 }
 
@@ -297,10 +352,12 @@ __device__ void qr_apply_block(const double* __restrict__ v, double tau, double*
 }
 
 // Dynamic shared memory: n doubles for the current reflector, plus (when
-// cols_in_smem) ceil(n / gridDim.x) * n doubles holding this CTA's columns.
+// cols_in_smem) ceil(n / gridDim.x) * n doubles holding this CTA's columns,
+// which are copied to At once final.
 __global__ void __launch_bounds__(256) k_qr_cols(QRArgs q, int cols_in_smem) {
     extern __shared__ double qr_smem[];
     __shared__ double red[140];
+    __shared__ double s_tau;
     __shared__ int s_abort;
     const int n = q.n, G = gridDim.x, me = blockIdx.x;
     const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -309,6 +366,13 @@ __global__ void __launch_bounds__(256) k_qr_cols(QRArgs q, int cols_in_smem) {
     auto col = [&](int c) -> double* {
         return cols_in_smem ? cols + (size_t)((c - me) / G) * n : q.At + (size_t)c * n;
     };
+    auto store_final = [&](int c) {
+        if (cols_in_smem) {
+            const double* src = col(c);
+            double* g = q.At + (size_t)c * n;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) g[i] = src[i];
+        }
+    };
     if (threadIdx.x == 0) s_abort = 0;
     if (cols_in_smem)
         for (int c = me; c < n; c += G) {
@@ -316,34 +380,30 @@ __global__ void __launch_bounds__(256) k_qr_cols(QRArgs q, int cols_in_smem) {
             for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = q.At[(size_t)c * n + i];
         }
     __syncthreads();
+    const unsigned long long lim = wait_limit(q.st);
     if (me == 0) {
         qr_make_reflector(q, col(0), 0, red);
-        qr_publish(q, col(0), 0, cols_in_smem);
+        store_final(0);
     }
     for (int j = 0; j < n - 1; ++j) {
         if (threadIdx.x == 0) {
-            volatile unsigned int* f = q.flags + j;
-            const unsigned long long t0 = global_ns(), lim = wait_limit(q.st);
-            while (*f != q.epoch) {
-                if (*(volatile int*)&q.st->err) { s_abort = 1; break; }
-                if (global_ns() - t0 > lim) { flag_error(q.st, DERR_TIMEOUT, 101); s_abort = 1; break; }
-                __nanosleep(20);
-            }
-            __threadfence();
+            unsigned long long t;
+            if (await_published(q.pubx + j, t, q.st, lim, 101)) s_tau = __longlong_as_double((long long)t);
+            else s_abort = 1;
         }
         __syncthreads();
         if (s_abort) return;
-        const double* colj = q.At + (size_t)j * n;
-        const double tau = __ldcg(q.tau + j);
-        stage_column(colj, v, j + 1, n, j);
+        const double tau = s_tau;
+        if (!stage_published(q.pub + (size_t)j * n, v, j + 1, n, j, q.st, lim, 101)) s_abort = 1;
         if (threadIdx.x == 0) v[0] = 1.0;
         __syncthreads();
+        if (s_abort) return;
         // lookahead: the owner of column j+1 finishes it first and publishes it
         if ((j + 1) % G == me) {
             double* c1 = col(j + 1);
             if (tau != 0.0) qr_apply_block(v, tau, c1, j, n, red);
             if (j + 1 < n - 1) qr_make_reflector(q, c1, j + 1, red);
-            qr_publish(q, c1, j + 1, cols_in_smem);
+            store_final(j + 1);
         }
         if (tau != 0.0) {
             int cnt = 0;
@@ -404,7 +464,8 @@ __device__ __forceinline__ void store_vec(double* dst, int lo, int hi, const dou
 // (array At), P A = L U: on exit L (unit lower, below the diagonal) and U
 // (upper, with the diagonal) overwrite At, piv[j] is the row swapped with row j
 // at step j.  Cooperative launch, the same column ownership, shared-memory
-// column storage and flag protocol as k_qr_cols; the critical path of a step
+// column storage and publication hand-off as k_qr_cols (the scalar of step j is
+// the pivot row, stored as the bits of an integer); the critical path of a step
 // holds one reduction (the pivot search) instead of the two of a Householder
 // step.
 // In At the multipliers of column j stay in the row order of step j (the
@@ -417,14 +478,14 @@ __device__ __forceinline__ void store_vec(double* dst, int lo, int hi, const dou
 // factorisation.
 // ---------------------------------------------------------------------------
 struct LUArgs {
-    double* At; int* piv; unsigned int* flags; unsigned int epoch; int n;
+    double* At; int* piv; double* pub; double* pubx; int n;
     DevStatus* st;
     double* Fr; int* lperm;     // optional (both or neither)
 };
 
-// pivot search, swap and scaling of column j (rows j..n-1), whole CTA (256
-// threads).  Magnitudes are compared as the integer images of |x| (ties to the
-// smaller row, a NaN wins and is flagged), so the search uses no FP64
+// pivot search, swap, scaling and publication of column j (rows j..n-1), whole
+// CTA (256 threads).  Magnitudes are compared as the integer images of |x| (ties
+// to the smaller row, a NaN wins and is flagged), so the search uses no FP64
 // instruction; one thread forms the pivot's reciprocal.
 __device__ void lu_pivot_column(const LUArgs& q, double* col, int j, double* redv, int* redi) {
     const int n = q.n;
@@ -451,30 +512,20 @@ __device__ void lu_pivot_column(const LUArgs& q, double* col, int j, double* red
         col[j] = col[bi];
         col[bi] = t;
         const double pv = col[j];
-        redv[32] = pv;
-        redi[32] = bi;
         q.piv[j] = bi;
+        st_relaxed_b64(q.pubx + j, (unsigned long long)bi);
         if (best <= 0 || !finite_bits(pv)) flag_error(q.st, DERR_NUMERIC, 110);
         redv[33] = recip_fast(pv);
     }
     __syncthreads();
     const double inv = redv[33];
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) col[i] *= inv;
-    __syncthreads();
-}
-
-__device__ void lu_publish(const LUArgs& q, const double* col, int j, bool copy) {
-    double* g = q.At + (size_t)j * q.n;
-    if (copy)
-        for (int i = threadIdx.x; i < q.n; i += blockDim.x) g[i] = col[i];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicExch(&q.flags[j], q.epoch);
+    double* pj = q.pub + (size_t)j * n;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+        const double x = col[i] * inv;
+        col[i] = x;
+        st_relaxed_f64(pj + i, x);
     }
-    // the row-major copy is read only after the kernel: written after the flag
-    if (q.Fr)
-        for (int i = threadIdx.x; i < q.n; i += blockDim.x) q.Fr[(size_t)i * q.n + j] = col[i];
+    __syncthreads();
 }
 
 // apply step j (swap rows j, p; a_i -= l_ij a_j for i > j) to a column; one warp
@@ -503,6 +554,16 @@ __global__ void __launch_bounds__(256) k_lu_cols(LUArgs q, int cols_in_smem) {
     auto col = [&](int c) -> double* {
         return cols_in_smem ? cols + (size_t)((c - me) / G) * n : q.At + (size_t)c * n;
     };
+    // a finished column: to At (when held in shared memory) and to the row-major factor
+    auto store_final = [&](int c) {
+        const double* src = col(c);
+        if (cols_in_smem) {
+            double* g = q.At + (size_t)c * n;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) g[i] = src[i];
+        }
+        if (q.Fr)
+            for (int i = threadIdx.x; i < n; i += blockDim.x) q.Fr[(size_t)i * n + c] = src[i];
+    };
     if (threadIdx.x == 0) s_abort = 0;
     if (cols_in_smem)
         for (int c = me; c < n; c += G) {
@@ -512,20 +573,16 @@ __global__ void __launch_bounds__(256) k_lu_cols(LUArgs q, int cols_in_smem) {
     if (me == 0 && q.lperm)
         for (int i = threadIdx.x; i < n; i += blockDim.x) q.lperm[i] = i;
     __syncthreads();
+    const unsigned long long lim = wait_limit(q.st);
     if (me == 0) {
         lu_pivot_column(q, col(0), 0, redv, redi);
-        lu_publish(q, col(0), 0, cols_in_smem);
+        store_final(0);
     }
     for (int j = 0; j < n - 1; ++j) {
         if (threadIdx.x == 0) {
-            volatile unsigned int* f = q.flags + j;
-            const unsigned long long t0 = global_ns(), lim = wait_limit(q.st);
-            while (*f != q.epoch) {
-                if (*(volatile int*)&q.st->err) { s_abort = 1; break; }
-                if (global_ns() - t0 > lim) { flag_error(q.st, DERR_TIMEOUT, 111); s_abort = 1; break; }
-            }
-            __threadfence();
-            s_piv = *(volatile int*)(q.piv + j);
+            unsigned long long t;
+            if (await_published(q.pubx + j, t, q.st, lim, 111)) s_piv = (int)t;
+            else s_abort = 1;
         }
         __syncthreads();
         if (s_abort) return;
@@ -545,9 +602,9 @@ __global__ void __launch_bounds__(256) k_lu_cols(LUArgs q, int cols_in_smem) {
                 q.lperm[p] = a;
             }
         }
-        const double* colj = q.At + (size_t)j * n;
-        stage_column(colj, l, j + 1, n, 0);
+        if (!stage_published(q.pub + (size_t)j * n, l, j + 1, n, 0, q.st, lim, 111)) s_abort = 1;
         __syncthreads();
+        if (s_abort) return;
         // lookahead: the owner of column j+1 finishes it first and publishes it
         if ((j + 1) % G == me) {
             double* c1 = col(j + 1);
@@ -562,7 +619,7 @@ __global__ void __launch_bounds__(256) k_lu_cols(LUArgs q, int cols_in_smem) {
             __syncthreads();
             if (j + 1 < n - 1) lu_pivot_column(q, c1, j + 1, redv, redi);
             else if (threadIdx.x == 0) q.piv[j + 1] = j + 1;
-            lu_publish(q, c1, j + 1, cols_in_smem);
+            store_final(j + 1);
         }
         int cnt = 0;
         for (int c = j + 2 + ((me - (j + 2)) % G + G) % G; c < n; c += G, ++cnt)
