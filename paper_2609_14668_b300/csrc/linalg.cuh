@@ -676,7 +676,10 @@ __global__ void __launch_bounds__(256) k_fwdsolve_perm(const double* __restrict_
 // Form columns of Q = H_0 ... H_{n-2} (Qt rows), each multiplied by sgn[c]:
 // column c starts as e_c and takes H_j for j = min(c, n-2) down to 0.  Column c
 // needs about 2 c n FMAs, so the columns of a CTA are taken cyclically
-// (b, b + G, b + 2G, ...) to give every CTA the same mix of short and long ones.
+// (b, b + G, b + 2G, ...) to give every CTA the same mix of short and long ones,
+// and with eight columns warps w and w + 4 (which share a sub-partition and its
+// FP64 unit) take columns k = w and k = 7 - w of that list: a short one with a
+// long one on every sub-partition.
 template <int CPB_, int PRE_>
 __global__ void __launch_bounds__(256) k_form_q(const double* __restrict__ Vt, const double* __restrict__ tau,
                                                 const double* __restrict__ sgn, double* Qt, int n) {
@@ -684,7 +687,8 @@ __global__ void __launch_bounds__(256) k_form_q(const double* __restrict__ Vt, c
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double* vbuf = cs_smem;
     double* col = cs_smem + n + (size_t)(warp < CPB_ ? warp : 0) * n;
-    const int c = blockIdx.x + gridDim.x * warp;
+    const int kk = (CPB_ == 8 && warp >= 4) ? 11 - warp : warp;
+    const int c = blockIdx.x + gridDim.x * kk;
     const bool has = warp < CPB_ && c < n;
     if (warp < CPB_)
         for (int i = lane; i < n; i += 32) col[i] = (i == c) ? 1.0 : 0.0;
