@@ -491,7 +491,7 @@ void solve_blocked(afqmc_handle* h, const double* Fr, const double* in, const do
 
 // dynamic shared memory of k_update_slice: window block (phase B) or flush tiles (phase F)
 size_t update_smem(int W, int nd, int precision, int N = AFQMC_NOALLOC_MAX_N, int grid = 148) {
-    size_t b = sizeof(double) * ((size_t)W * (W + 1) + 5 * W);
+    size_t b = sizeof(double) * (2 * (size_t)W * (W + 1) + 6 * W);
     const size_t jpb = (size_t)((N + grid - 1) / grid);
     b = std::max(b, sizeof(double) * (2 * (size_t)nd * jpb + 2 * (size_t)nd * W + 2 * (size_t)W * W));   // phase C staging
     size_t f = sizeof(double) * 2 * (size_t)nd * 32;

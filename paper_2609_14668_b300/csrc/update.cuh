@@ -346,7 +346,9 @@ __global__ void __launch_bounds__(UPD_THREADS, 3) k_update_slice(UpdArgs a) {
             double* dd = vv + W;                          // W values of Delta
             double* od = dd + W;                          // W values of 1 + Delta (charge: Im Delta)
             double* xs = od + W;                          // W: x of the current move at the window positions
-            int8_t* sw = reinterpret_cast<int8_t*>(xs + W); // W field values
+            int8_t* sw = reinterpret_cast<int8_t*>(xs + W); // W field values (W doubles reserved), then
+                                                          // the second W x (W+1) block and a second x
+                                                          // vector (W) of the spin-channel path
             __shared__ int s_found[2];
             __shared__ double s_c[2], s_c2[2];
             const int nw = win_len(a, cursor);
@@ -395,8 +397,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 3) k_update_slice(UpdArgs a) {
                 // its accept test and the coefficient Delta / r computed ahead of
                 // time.  A ballot over the positions not yet visited names the next
                 // accepted site at once, so no thread walks the rejected sites one
-                // by one; each value has the arithmetic of the serial scan below,
-                // so the decisions and the block are the same.
+                // by one.
                 // On this part every FP64 warp instruction holds its sub-partition's
                 // FP64 unit for ~64 cycles whatever the number of active lanes, so
                 // the decision chain is written with as few of them as possible:
@@ -404,69 +405,142 @@ __global__ void __launch_bounds__(UPD_THREADS, 3) k_update_slice(UpdArgs a) {
                 // by -c G(q,tf) G(tf,q) (c = Delta / r of that move, the diagonal
                 // change times Delta); the test r^2 > v reads rr^2 > v / Delta^2 and
                 // the coefficient Delta / r of lane q is 1 / rr.  Delta = 0 (U = 0):
-                // r = 1 and c = 0.
+                // r = 1 and c = 0.  (The values follow the serial scan below up to
+                // the rounding of these reformulations.)
+                // Pipeline.  The block after a accepted moves, G^(a), lives in
+                // buffer a & 1 (Gw, Gw2).  Warps 1-7 form G^(a+1) (the trailing
+                // rank-1 update of move a, off the diagonal) into the other buffer
+                // while warp 0 already decides the next move: it needs only column
+                // and row t' of G^(a+1) for the next accepted site t', which it forms
+                // itself from G^(a) and the rank-1 term of move a (the same FMAs as
+                // the trailing update, so the values are identical).  So the
+                // trailing update runs one move behind and leaves the decision chain.
+                // Hand-offs are named barriers, each used on alternate moves so that
+                // no barrier is arrived at twice before its phase completes:
+                //   TF (2, 3): warp 0 publishes move a (site, c, and its x at the
+                //     window positions; site -1 ends the window) and arrives; warps
+                //     1-7 wait.  Warp 0 publishes move a+1 only after it has read G^(a)
+                //     (which move a+1 overwrites).
+                //   DONE (4, 5): warps 1-7 arrive when G^(a+1) is complete; warp 0
+                //     waits before reading it (one move later), and once at the end.
                 const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-                double rr = 0.0, sq = 0.0, cq = 0.0;
-                bool okq = false, dz = false;
-                auto test = [&]() {     // r^2 > v  <=>  |rr| > sqrt(v) / |Delta| = sq
-                    if (dz) return;
-                    if (!finite_bits(rr)) { flag_error(a.st, DERR_NUMERIC, 200); okq = false; cq = 0.0; return; }
-                    okq = abs_gt(rr, sq);
-                    cq = recip_fast(rr);
-                };
-                if (warp == 0 && lane < nw) {
-                    const double dq = dd[lane];
-                    dz = dq == 0.0;
-                    if (dz) {
-                        okq = 1.0 > vv[lane];
-                    } else {
-                        const double inv = 1.0 / dq;
-                        rr = fma(-dq, Gw[lane * ld + lane], od[lane]) * inv;
-                        sq = sqrt(vv[lane]) * fabs(inv);
-                        test();
-                    }
-                }
-                for (;; ++it) {
-                    const int slot = it & 1;
-                    if (warp == 0) {
-                        const unsigned m = __ballot_sync(0xffffffffu, okq && lane >= t0 && lane < nw);
-                        const int tf = m ? __ffs((int)m) - 1 : -1;
-                        const double c = __shfl_sync(0xffffffffu, cq, tf >= 0 ? tf : 0);
-                        if (lane == 0) { s_found[slot] = tf; s_c[slot] = c; }
-                    }
-                    __syncthreads();
-                    const int tf = s_found[slot];
-                    if (tf < 0) break;
-                    const double c = s_c[slot];
-                    const int rest = nw - tf - 1;
-                    if (warp == 0) {
-                        if (lane > tf && lane < nw && !dz) {
-                            rr = fma(-c, Gw[lane * ld + tf] * Gw[tf * ld + lane], rr);
+                double* Gw2 = xs + 2 * W;                          // second block buffer, after sw
+                double* xsb[2] = {xs, Gw2 + W * ld};               // x of move a at the window positions, by a & 1
+                __shared__ int s_tf[2];
+                __shared__ double s_cc[2];
+                if (warp == 0) {
+                    double rr = 0.0, sq = 0.0, cq = 0.0;
+                    bool okq = false, dz = false;
+                    auto test = [&]() {     // r^2 > v  <=>  |rr| > sqrt(v) / |Delta| = sq
+                        if (dz) return;
+                        if (!finite_bits(rr)) { flag_error(a.st, DERR_NUMERIC, 200); okq = false; cq = 0.0; return; }
+                        okq = abs_gt(rr, sq);
+                        cq = recip_fast(rr);
+                    };
+                    if (lane < nw) {
+                        const double dq = dd[lane];
+                        dz = dq == 0.0;
+                        if (dz) {
+                            okq = 1.0 > vv[lane];
+                        } else {
+                            const double inv = 1.0 / dq;
+                            rr = fma(-dq, Gw[lane * ld + lane], od[lane]) * inv;
+                            sq = sqrt(vv[lane]) * fabs(inv);
                             test();
                         }
-                    } else {
-                        // x of the move at the later window positions (warp 1), for the
-                        // trailing update
-                        if (warp == 1 && lane < rest) xs[tf + 1 + lane] = c * Gw[(tf + 1 + lane) * ld + tf];
-                        asm volatile("bar.sync 1, %0;" :: "r"(UPD_THREADS - 32) : "memory");
+                    }
+                    // first accepted site, its column and row of G^(0)
+                    unsigned m = __ballot_sync(0xffffffffu, okq && lane < nw);
+                    int tf = m ? __ffs((int)m) - 1 : -1;
+                    double c = __shfl_sync(0xffffffffu, cq, tf >= 0 ? tf : 0);
+                    double col = 0.0, row = 0.0;
+                    if (tf >= 0 && lane < nw) { col = Gw[lane * ld + tf]; row = Gw[tf * ld + lane]; }
+                    double xq = c * col;                            // x of the move at position q
+                    if (lane < nw) xsb[0][lane] = xq;
+                    if (lane == 0) { s_tf[0] = tf; s_cc[0] = c; }
+                    asm volatile("bar.arrive 2, %0;" :: "r"(UPD_THREADS) : "memory");
+                    int na = 0;
+                    while (tf >= 0) {
+                        // move na at tf: the later diagonal entries, their tests
+                        // (rr -= c G(q,tf) G(tf,q) as x_q G(tf,q), x_q = c G(q,tf))
+                        if (lane > tf && lane < nw && !dz) {
+                            rr = fma(-xq, row, rr);
+                            test();
+                        }
+                        ++kk;
+                        int tn = -1;
+                        double cn = 0.0;
+                        if (kk == nd) {
+                            tstop = tf + 1;
+                        } else {
+                            m = __ballot_sync(0xffffffffu, okq && lane > tf && lane < nw);
+                            tn = m ? __ffs((int)m) - 1 : -1;
+                            cn = __shfl_sync(0xffffffffu, cq, tn >= 0 ? tn : 0);
+                        }
+                        // G^(na) complete (warps 1-7 finished move na-1)
+                        if (na >= 1) {
+                            if ((na - 1) & 1) asm volatile("bar.sync 5, %0;" :: "r"(UPD_THREADS) : "memory");
+                            else asm volatile("bar.sync 4, %0;" :: "r"(UPD_THREADS) : "memory");
+                        }
+                        double coln = 0.0, rown = 0.0;
+                        if (tn >= 0) {
+                            // column and row tn of G^(na+1) = G^(na) + x (row tf of G^(na))
+                            const double* B = (na & 1) ? Gw2 : Gw;
+                            const double rtn = __shfl_sync(0xffffffffu, row, tn);   // G^(na)(tf, tn)
+                            const double xtn = __shfl_sync(0xffffffffu, xq, tn);    // x at tn
+                            if (lane < nw) {
+                                coln = fma(xq, rtn, B[lane * ld + tn]);
+                                rown = fma(xtn, row, B[tn * ld + lane]);
+                            }
+                        }
+                        // publish move na+1 (or the end); G^(na) has been read
+                        const int ns = (na + 1) & 1;
+                        const double xn = cn * coln;
+                        if (tn >= 0 && lane < nw) xsb[ns][lane] = xn;
+                        if (lane == 0) { s_tf[ns] = tn; s_cc[ns] = cn; }
+                        if (ns) asm volatile("bar.arrive 3, %0;" :: "r"(UPD_THREADS) : "memory");
+                        else asm volatile("bar.arrive 2, %0;" :: "r"(UPD_THREADS) : "memory");
+                        tf = tn;
+                        c = cn;
+                        col = coln;
+                        row = rown;
+                        xq = xn;
+                        ++na;
+                    }
+                    if (na >= 1) {
+                        if ((na - 1) & 1) asm volatile("bar.sync 5, %0;" :: "r"(UPD_THREADS) : "memory");
+                        else asm volatile("bar.sync 4, %0;" :: "r"(UPD_THREADS) : "memory");
+                    }
+                } else {
+                    for (int na = 0;; ++na) {
+                        const int sl = na & 1;
+                        if (sl) asm volatile("bar.sync 3, %0;" :: "r"(UPD_THREADS) : "memory");
+                        else asm volatile("bar.sync 2, %0;" :: "r"(UPD_THREADS) : "memory");
+                        const int tf = s_tf[sl];
+                        if (tf < 0) break;
+                        const double c = s_cc[sl];
+                        const double* src = sl ? Gw2 : Gw;
+                        double* dst = sl ? Gw : Gw2;
+                        const double* xv = xsb[sl];
+                        const int rest = nw - tf - 1;
                         if (warp == 4) {
                             // the move and its x, y at the later window positions, to
                             // the recursion of phase C (global stores, off the FP64 warps)
+                            const int km = k + na;
                             if (lane == 0) {
-                                a.msite[kk] = cursor + tf;
-                                a.mcoef[kk] = c;
+                                a.msite[km] = cursor + tf;
+                                a.mcoef[km] = c;
                                 a.s[cursor + tf] = (int8_t)(-sw[tf]);
                             }
                             if (lane < rest) {
                                 const int q = tf + 1 + lane;
-                                a.xw[kk * W + q] = xs[q];
-                                a.yw[kk * W + q] = -Gw[tf * ld + q];
+                                a.xw[km * W + q] = xv[q];
+                                a.yw[km * W + q] = -src[tf * ld + q];
                             }
                         } else {
-                            // the off-diagonal trailing block, G(q,p) += x_q G(tf,p) for
-                            // q, p > tf (column and row tf are read only), packed 32
-                            // entries per warp instruction over warps 1-3 and 5-7 (warp 4
-                            // shares warp 0's sub-partition and stays off FP64)
+                            // G^(na+1)(q,p) = G^(na)(q,p) + x_q G^(na)(tf,p) for q != p > tf,
+                            // packed 32 entries per warp instruction over warps 1-3 and 5-7
+                            // (warp 4 shares warp 0's sub-partition and stays off FP64)
                             const int wr = warp < 4 ? warp - 1 : warp - 2;      // 0..5
                             const int tot = rest * rest;
                             const float rinv = 1.0f / (float)max(rest, 1);
@@ -484,16 +558,15 @@ __global__ void __launch_bounds__(UPD_THREADS, 3) k_update_slice(UpdArgs a) {
                                 int q1 = 0, p1 = 0, q2 = 0, p2 = 0;
                                 const bool h1 = e1 < tot, h2 = e2 < tot;
                                 double x1 = 0.0, y1 = 0.0, g1 = 0.0, x2 = 0.0, y2 = 0.0, g2 = 0.0;
-                                if (h1) { split(e1, q1, p1); x1 = xs[q1]; y1 = Gw[tf * ld + p1]; g1 = Gw[q1 * ld + p1]; }
-                                if (h2) { split(e2, q2, p2); x2 = xs[q2]; y2 = Gw[tf * ld + p2]; g2 = Gw[q2 * ld + p2]; }
-                                if (h1 && q1 != p1) Gw[q1 * ld + p1] = fma(x1, y1, g1);
-                                if (h2 && q2 != p2) Gw[q2 * ld + p2] = fma(x2, y2, g2);
+                                if (h1) { split(e1, q1, p1); x1 = xv[q1]; y1 = src[tf * ld + p1]; g1 = src[q1 * ld + p1]; }
+                                if (h2) { split(e2, q2, p2); x2 = xv[q2]; y2 = src[tf * ld + p2]; g2 = src[q2 * ld + p2]; }
+                                if (h1 && q1 != p1) dst[q1 * ld + p1] = fma(x1, y1, g1);
+                                if (h2 && q2 != p2) dst[q2 * ld + p2] = fma(x2, y2, g2);
                             }
                         }
+                        if (sl) asm volatile("bar.arrive 5, %0;" :: "r"(UPD_THREADS) : "memory");
+                        else asm volatile("bar.arrive 4, %0;" :: "r"(UPD_THREADS) : "memory");
                     }
-                    t0 = tf + 1;
-                    ++kk;
-                    if (kk == nd) { tstop = tf + 1; break; }
                 }
             } else
             for (;; ++it) {
