@@ -69,7 +69,10 @@ __device__ __forceinline__ bool grid_barrier(DevStatus* st, int where) {
         } else {
             const unsigned long long t0 = global_ns(), lim = wait_limit(st);
             unsigned int nap = 32;     // back-off: the waiting CTAs poll one L2 line while
-                                       // the working ones need the memory system
+                                       // the working ones need the memory system; capped
+                                       // at 128 ns (147 CTAs polling at that rate are ~1e9
+                                       // loads/s, while each wait at the cap costs ~64 ns
+                                       // of latency on average after the last arrival)
             for (;;) {
                 unsigned int g;
                 asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(genp) : "memory");
@@ -80,7 +83,7 @@ __device__ __forceinline__ bool grid_barrier(DevStatus* st, int where) {
                     break;
                 }
                 __nanosleep(nap);
-                if (nap < 512) nap <<= 1;
+                if (nap < 128) nap <<= 1;
             }
         }
         s_ok = (*(volatile int*)&st->err) == 0;
