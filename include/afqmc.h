@@ -158,12 +158,22 @@ afqmc_status afqmc_set_field(afqmc_handle* h, const int8_t* s_host, uint64_t swe
 /* Copy the current field to host (M*N int8). */
 afqmc_status afqmc_get_field(afqmc_handle* h, int8_t* s_host);
 
+/* Sanity limit on the stabilisation drift: at a recomputation of G, an element of
+ * the wrapped G that differs from the recomputed one by more than
+ * AFQMC_DRIFT_LIMIT * max(1, |G_ij|) makes the sweep fail with AFQMC_E_NUMERIC
+ * (the chain no longer samples Eq. ConfgWeight).  The FP64 path drifts by ~1e-8
+ * at L = 24, n_stab = 8; the split-TF32 flush by up to ~0.5 in the worst element
+ * of long runs. */
+#define AFQMC_DRIFT_LIMIT 10.0
+
 /* Run n_sweeps sweeps (Sec. III.A: a forward pass l = 1..M and a backward pass
  * l = M..1; in each slice every site i = 0..N-1 is proposed once, accepted iff
  * u < R with R = e^{2 gamma s_i} |r|^2 (spin channel) or |r|^2 (charge channel),
  * r = 1 + Delta (1 - G_ii), Delta = e^{-2 gamma s_i} - 1 (gamma = gamma_s or
  * gamma_c), using the delayed update of rank n_delay; G recomputed every
- * n_stab slices).  stats may be NULL. */
+ * n_stab slices).  stats may be NULL.  AFQMC_E_NUMERIC on a non-finite value
+ * or a drift above AFQMC_DRIFT_LIMIT; AFQMC_E_TIMEOUT when a device wait runs
+ * out. */
 afqmc_status afqmc_sweep(afqmc_handle* h, int32_t n_sweeps, afqmc_sweep_stats* stats);
 
 /* Measure the current G (the slice the chain is at: slice 0 between sweeps) now.

@@ -675,7 +675,7 @@ void recompute(afqmc_handle* h, int c) {
     double* saved = h->Wk[5];
     CK(cudaMemcpyAsync(saved, h->G, sizeof(double) * nn, cudaMemcpyDeviceToDevice, h->stream));
     form_green(h, h->Rst[c], h->Lst[c], h->G);
-    { Scope sc(h, AFQMC_K_MISC); k_maxabsdiff<<<h->sms * 2, 256, 0, h->stream>>>(h->G, saved, nn, h->drift, h->st); }
+    { Scope sc(h, AFQMC_K_MISC); k_maxabsdiff<<<h->sms * 2, 256, 0, h->stream>>>(h->G, saved, nn, h->drift, h->st, AFQMC_DRIFT_LIMIT); }
     CK(cudaGetLastError());
     if (h->p.measure) measure(h, h->G, true);
 }
@@ -691,6 +691,11 @@ afqmc_status check_device(afqmc_handle* h) {
     CK(cudaStreamSynchronize(h->stream));
     DevStatus st;
     CK(cudaMemcpy(&st, h->st, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st.err == DERR_NUMERIC && st.where == 107) {
+        set_error(h, AFQMC_E_NUMERIC, "stabilisation drift above the limit: an element of the wrapped G differs from "
+                                      "the recomputed one by more than AFQMC_DRIFT_LIMIT max(1, |G_ij|) (site code 107)");
+        return AFQMC_E_NUMERIC;
+    }
     if (st.err == DERR_NUMERIC) {
         set_error(h, AFQMC_E_NUMERIC, "non-finite value in device computation (site code " + std::to_string(st.where) + ")");
         return AFQMC_E_NUMERIC;

@@ -846,18 +846,23 @@ __global__ void k_check_finite(const double* __restrict__ A, size_t len, DevStat
 }
 
 // max |A - B| (elementwise) and NaN detection -> out[0] (atomic max on the bit pattern of a non-negative double).
+// A is the recomputed G, B the wrapped one: an element with |A - B| > limit max(1, |A|)
+// flags DERR_NUMERIC (site 107): the chain no longer samples its weight.
 __global__ void k_maxabsdiff(const double* __restrict__ A, const double* __restrict__ B, size_t len,
-                             unsigned long long* out, DevStatus* st) {
+                             unsigned long long* out, DevStatus* st, double limit) {
     double m = 0.0;
-    bool bad = false;
+    bool bad = false, over = false;
     for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < len; o += (size_t)gridDim.x * blockDim.x) {
-        const double d = fabs(A[o] - B[o]);
-        if (!isfinite(A[o])) bad = true;
+        const double a = A[o];
+        const double d = fabs(a - B[o]);
+        if (!isfinite(a)) bad = true;
+        if (d > limit * fmax(1.0, fabs(a))) over = true;
         m = fmax(m, d);
     }
     m = warp_max(m);
     if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) flag_error(st, DERR_NUMERIC, 104);
+    if (__any_sync(0xffffffffu, over) && (threadIdx.x & 31) == 0) flag_error(st, DERR_NUMERIC, 107);
 }
 
 }  // namespace afq

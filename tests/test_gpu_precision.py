@@ -102,3 +102,20 @@ def test_tf32_equilibrium_matches_fp64_within_two_sigma(pkg):
         print(f"TF32_VS_FP64 L=6 {k}: tf32 {a.mean():.6f} fp64 {b.mean():.6f} diff {a.mean() - b.mean():+.2e} "
               f"+- {sd:.1e} z = {z:+.2f}")
         assert abs(z) < 2.0, (k, a.mean(), b.mean(), sd)
+
+
+@pytest.mark.parametrize("precision,n_stab,bound", [(3, 8, 1.0), (3, 1, 1e-3), (0, 8, 1e-7)])
+def test_stabilisation_drift_stays_bounded(pkg, precision, n_stab, bound):
+    """max |G_wrapped - G_recomputed| over 6 sweeps (after 2) of one chain at
+    L = 12, beta t = 12, n_d = 32.  Measured on the B300: 8.7e-3 with the
+    split-TF32 flush at n_stab = 8 (0.21 the worst over 16 chains x 200
+    sweeps), 7.8e-6 at n_stab = 1, 1.5e-10 for FP64 at n_stab = 8.  The bounds
+    hold the order of magnitude with a wide margin, so that a flush or a wrap
+    that lost accuracy fails here; the library's own gate (AFQMC_DRIFT_LIMIT,
+    10 max(1, |G_ij|) per element) sits far above all of them."""
+    ch = pkg.Chain(pkg.make_params(L=12, beta=12.0, dtau=0.1, U=3.73, n_delay=32, n_stab=n_stab, seed=77,
+                                   precision=precision))
+    ch.sweep(2)
+    worst = max(ch.sweep(1).max_stab_drift for _ in range(6))
+    assert 0.0 <= worst < bound, worst
+    ch.close()
