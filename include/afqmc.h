@@ -13,7 +13,7 @@
  *   - Metropolis updates with determinant ratios and the delayed rank-k
  *     Green's-function update: Sec. III.B, Eqs. DetailBalance, DRatio,
  *     rRatioLocal, DelayG0, DelayRatio, DelayRgenk, FinalDelay;
- *   - periodic QR stabilisation of the propagator chains: Sec. II.B ('Second');
+ *   - periodic QR stabilisation of the propagator chains: Sec. II.B (second note);
  *   - equal-time observables: Sec. II.C, App. C.
  *
  * Conventions shared by every entry point

@@ -4,7 +4,7 @@ bonds, complex G), with the Ising field in the spin channel (HS-s^z, Eq. SzHS)
 or in the charge channel (HS-n, Eq. DensityHS).
 
 Follows Sec. II.B (Eqs. SzHS, DensityHS, coupling, BIOpSz, BIOpnT,
-ConfgWeight, GrFMat and the implementation notes 'First'..'Fifth') and
+ConfgWeight, GrFMat and its five implementation notes) and
 Sec. III.B (Eqs. DetailBalance, DRatio, GFupdate, rRatioLocal, GupdateLocal,
 DelayG0, DelayRatio, DelayRgenk, FinalDelay).  Propagators are dense:
 B_l = e^{lambda diag(s_l)} E with E = e^{-dtau H0} from a Taylor series (no

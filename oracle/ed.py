@@ -3,7 +3,7 @@ for small clusters, used to pin the oracle's weights and Wick contractions.
 
 Two forms:
   * ``trotter_averages``: the Trotterised density matrix
-    rho = (e^{-dtau H0/2} e^{-dtau H_U} e^{-dtau H0/2})^M  (Sec. II.B 'First'),
+    rho = (e^{-dtau H0/2} e^{-dtau H_U} e^{-dtau H0/2})^M  (first implementation note of Sec. II.B),
     which the Hubbard-Stratonovich sum reproduces exactly at any dtau;
   * ``thermal_averages``: exact e^{-beta H} by full diagonalisation (tiny clusters).
 

@@ -6,8 +6,8 @@
   touches the momentum-space form of Sec. III.A, so the FFT propagation of the
   CUDA path is checked against an independent construction.
 * ``udt``: A = U D T with U orthogonal, D > 0 diagonal, T = D^-1 R P^T from a
-  column-pivoted Householder QR (scipy/LAPACK geqp3).  This is the "QR
-  algorithm" stabilisation named in Sec. II.B ('Second').
+  column-pivoted Householder QR (scipy/LAPACK geqp3): the QR stabilisation of
+  the second implementation note of Sec. II.B.
 * ``stable_green``: G = (1 + R L)^-1 from R = U_R D_R T_R and L^T = U_L D_L T_L,
   by the large/small scale split of Loh & Gubernatis (1992) as written out in
   Bauer, SciPost Phys. Core 2, 011 (2020).

@@ -4,7 +4,7 @@ Input: the spin-up Green's function G_ij = <c_i c_j^+> at a slice boundary of
 the asymmetric Trotter product.  Readings:
   * observables are taken on G_sym = e^{-dtau H0/2} G e^{+dtau H0/2}, the
     Green's function of the symmetric third-order split used in production
-    (Sec. II.B 'First'); the weights of the two splits are identical;
+    (the first implementation note of Sec. II.B); the weights of the two splits are identical;
   * spin down follows from the partial particle-hole transform with the
     staggered sign kept:  G_dn_ij = (-1)^{i+j} (delta_ij - conj(G_up_ji));
   * Wick:  <n_ia n_jb> = n_ia n_jb + delta_ab (delta_ij - G^a_ji) G^a_ij,

@@ -1,17 +1,19 @@
-// FP64 dense linear algebra for the QR stabilisation of Sec. II.B ('Second')
-// and the recomputation of G = (1 + R L)^-1 (Eq. GrFMat).
+// FP64 dense linear algebra for the QR stabilisation of Sec. II.B (its second
+// implementation note) and the recomputation of G = (1 + R L)^-1 (Eq. GrFMat).
 //
 // B300 design notes.  FP64 runs at ~1.1 TFLOP/s on this part (SIMT DFMA is a
 // little faster than the FP64 tensor path, DMMA), so every kernel here is
 // bound by the FP64 pipes, not by memory: the working matrices (10.6 MB at
 // N = 1152) stay resident in the 126 MB L2.  The kernels therefore aim at
 // keeping all 148 SMs' FP64 units busy:
-//   * k_dgemm: 64x64 register-tiled SIMT GEMM with row/column scaling epilogue;
-//   * k_qr_cols: Householder QR as one cooperative kernel, columns owned
-//     cyclically by CTAs, reflector j published through a flag and applied by
-//     every CTA to its own columns (one-column lookahead on the critical path);
+//   * k_dgemm: SIMT GEMM on 32x32 output tiles with a row/column scaling epilogue;
+//   * k_qr_cols, k_lu_cols: Householder QR and LU with partial pivoting as
+//     cooperative kernels, columns owned cyclically by CTAs, column j handed on
+//     through publication buffers (no flag, no fence) and applied by every CTA
+//     to its own columns (one-column lookahead on the critical path);
 //   * column-parallel kernels (one warp per column, no inter-CTA sync) for
-//     forming Q and the triangular solves.
+//     forming Q and the triangular solves; the blocked solves' diagonal blocks
+//     (k_trsm_leaf).
 // Matrices are row-major; a "column-major" matrix X is stored as its
 // transpose Xt (row c of Xt = column c of X).
 #pragma once
